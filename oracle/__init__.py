@@ -1,0 +1,244 @@
+"""CPU oracle for the superstep-scheduled sparse lower-triangular solve.
+
+TEST INFRASTRUCTURE ONLY.  Imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` -- never by the GPU library, which
+fails loudly when its CUDA extension is missing instead of falling back here.
+The oracle and the library share no code: only the seeded input generators in
+``workloads/`` feed both.
+
+What it computes (each function cites the passage it follows):
+
+* ``solve``          forward substitution, Eq. 2.1, sequential FP64 (C)
+* ``spmv``           y = A x in FP64 (C), for residual checks
+* ``levels``         wavefronts of the DAG of Sec. 2.2 / Fig. 1.1 (C)
+* ``growlocal``      the GrowLocal scheduler, Sec. 3 / Algorithm 3.1 (C)
+* ``level_schedule`` sigma = wavefront, pi = 0 (the wavefront scheduler, Sec. 1)
+* ``check_schedule`` Definition 2.1 plus the bookkeeping rules of a schedule
+* ``permutation``    the reordering of Sec. 5: sort by (superstep, core, id)
+* ``permute``        the symmetric permutation P A P^T of Sec. 5
+* ``validate``       input rules: square, lower, sorted, unique, diagonal last
+  and non-zero (Sec. 2.2 assumes a non-singular matrix)
+
+Pins (tests/test_oracle.py): the Fig. 1.1 worked example, dense triangular
+solves on tiny inputs, closed forms for diagonal and bidiagonal factors,
+closed-form wavefront counts of natural-order stencils, manufactured
+solutions, the hand-derived GrowLocal example on a diagonal matrix and brute
+force Definition 2.1 checks on small random DAGs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sptrsv_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle with gcc (no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_solve_fp64.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _f64p,
+                                              _f64p, ctypes.c_int64, _f64p, ctypes.c_int64]
+            lib.oracle_solve_fp64.restype = None
+            lib.oracle_spmv_fp64.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
+            lib.oracle_spmv_fp64.restype = None
+            lib.oracle_levels.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+            lib.oracle_levels.restype = ctypes.c_int32
+            lib.oracle_growlocal.argtypes = [ctypes.c_int32, _i32p, _i32p, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, _i32p, _i32p]
+            lib.oracle_growlocal.restype = ctypes.c_int32
+            _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _arrays(A):
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    c = np.ascontiguousarray(A.col, dtype=np.int32)
+    v = np.ascontiguousarray(A.val, dtype=np.float64)
+    return rp, c, v
+
+
+class InvalidFactor(ValueError):
+    pass
+
+
+def validate(A) -> None:
+    """Check the input rules of the problem (Sec. 2.2): lower-triangular CSR with
+    strictly increasing columns and a non-zero diagonal stored last in every row."""
+    n = A.n
+    rp, c, v = _arrays(A)
+    if rp.size != n + 1 or rp[0] != 0 or np.any(np.diff(rp) < 1) or rp[-1] != c.size:
+        raise InvalidFactor("bad row pointers (every row needs at least its diagonal)")
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    if np.any(c < 0) or np.any(c > rows):
+        raise InvalidFactor("entry above the diagonal or out of range")
+    same_row = rows[1:] == rows[:-1]
+    if np.any(same_row & (c[1:] <= c[:-1])):
+        raise InvalidFactor("columns not strictly increasing within a row")
+    last = rp[1:] - 1
+    if np.any(c[last] != np.arange(n)):
+        raise InvalidFactor("diagonal missing")
+    if np.any(v[last] == 0.0):
+        raise InvalidFactor("zero diagonal")
+
+
+def solve(A, b: np.ndarray) -> np.ndarray:
+    """Eq. 2.1 forward substitution in FP64; ``b`` is (n,) or (n, nrhs)."""
+    lib = _load()
+    rp, c, v = _arrays(A)
+    b2 = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(A.n, -1))
+    x = np.empty_like(b2, order="F")
+    lib.oracle_solve_fp64(A.n, b2.shape[1], _p(rp, _i32p), _p(c, _i32p), _p(v, _f64p),
+                          _p(b2, _f64p), A.n, _p(x, _f64p), A.n)
+    return x.reshape(np.shape(b)) if np.ndim(b) == 1 else x
+
+
+def spmv(A, x: np.ndarray) -> np.ndarray:
+    """y = A x in FP64 (every stored entry, diagonal included)."""
+    lib = _load()
+    rp, c, v = _arrays(A)
+    x2 = np.asfortranarray(np.asarray(x, dtype=np.float64).reshape(A.n, -1))
+    y = np.empty_like(x2, order="F")
+    for j in range(x2.shape[1]):
+        xj = np.ascontiguousarray(x2[:, j])
+        yj = np.empty(A.n)
+        lib.oracle_spmv_fp64(A.n, _p(rp, _i32p), _p(c, _i32p), _p(v, _f64p),
+                             _p(xj, _f64p), _p(yj, _f64p))
+        y[:, j] = yj
+    return y.reshape(np.shape(x)) if np.ndim(x) == 1 else y
+
+
+def levels(A):
+    """Wavefront index of every row (Fig. 1.1) and the number of wavefronts."""
+    lib = _load()
+    rp, c, _ = _arrays(A)
+    lv = np.empty(A.n, dtype=np.int32)
+    nlev = lib.oracle_levels(A.n, _p(rp, _i32p), _p(c, _i32p), _p(lv, _i32p))
+    return lv, int(nlev)
+
+
+def avg_wavefront(A) -> float:
+    """n divided by the length of the longest path (Sec. 6.2), counted in vertices."""
+    return A.n / max(1, levels(A)[1])
+
+
+def level_schedule(A):
+    """Wavefront schedule: superstep = wavefront, every vertex on core 0."""
+    lv, nlev = levels(A)
+    return lv, np.zeros(A.n, dtype=np.int32), nlev
+
+
+def growlocal(A, k: int, alpha0: float = 20.0, growth: float = 1.5, L: float = 500.0,
+              accept: float = 0.97):
+    """GrowLocal schedule (Algorithm 3.1): returns (sigma, pi, supersteps), 0-based."""
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    lib = _load()
+    rp, c, _ = _arrays(A)
+    sigma = np.empty(A.n, dtype=np.int32)
+    pi = np.empty(A.n, dtype=np.int32)
+    S = lib.oracle_growlocal(A.n, _p(rp, _i32p), _p(c, _i32p), int(k), float(alpha0),
+                             float(growth), float(L), float(accept), _p(sigma, _i32p),
+                             _p(pi, _i32p))
+    if S < 0:
+        raise MemoryError("oracle_growlocal failed")
+    return sigma, pi, int(S)
+
+
+def edges(A):
+    """DAG edges (j -> i) for every stored off-diagonal A_ij (Sec. 2.2)."""
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    off = A.col != rows
+    return A.col[off].astype(np.int64), rows[off]
+
+
+def check_schedule(A, sigma, pi, k: int, strict: bool = False) -> list[str]:
+    """Definition 2.1 and schedule bookkeeping; returns a list of violations.
+
+    * every vertex has one superstep sigma >= 0 and one core 0 <= pi < k;
+    * superstep numbers are contiguous 0..S-1;
+    * every edge (u, v): sigma(u) <= sigma(v), and sigma(u) < sigma(v) when
+      pi(u) != pi(v) (Def. 2.1); with ``strict`` every edge crosses a barrier
+      (the wavefront schedule).
+    """
+    sigma = np.asarray(sigma)
+    pi = np.asarray(pi)
+    bad = []
+    if sigma.shape != (A.n,) or pi.shape != (A.n,):
+        return ["schedule arrays have the wrong length"]
+    if A.n == 0:
+        return bad
+    if sigma.min() < 0:
+        bad.append("negative superstep")
+    if pi.min() < 0 or pi.max() >= k:
+        bad.append("core index out of range")
+    used = np.unique(sigma)
+    if used.size != sigma.max() + 1:
+        bad.append("superstep numbers not contiguous")
+    u, v = edges(A)
+    if np.any(sigma[u] > sigma[v]):
+        bad.append("edge goes to an earlier superstep")
+    cross = pi[u] != pi[v]
+    if np.any(cross & (sigma[u] >= sigma[v])):
+        bad.append("edge between cores inside a superstep")
+    if strict and np.any(sigma[u] >= sigma[v]):
+        bad.append("edge inside a superstep (wavefront schedule must be strict)")
+    return bad
+
+
+def permutation(sigma, pi) -> np.ndarray:
+    """Sec. 5 reordering: new position -> old row, sorted by (superstep, core, id)."""
+    sigma = np.asarray(sigma, dtype=np.int64)
+    pi = np.asarray(pi, dtype=np.int64)
+    ids = np.arange(sigma.size, dtype=np.int64)
+    return np.lexsort((ids, pi, sigma)).astype(np.int32)
+
+
+def permute(A, perm):
+    """Symmetric permutation P A P^T (row/col r of the result = row/col perm[r] of A),
+    returned as a dense-free (rows, cols, vals) triple in the new numbering."""
+    perm = np.asarray(perm, dtype=np.int64)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    return inv[rows], inv[A.col.astype(np.int64)], A.val.copy()
+
+
+def rel_error(x, xref) -> float:
+    """Normwise relative error max_i |x_i - xref_i| / max_i |xref_i|, worst column."""
+    x = np.asarray(x, dtype=np.float64).reshape(np.shape(xref)[0], -1)
+    xr = np.asarray(xref, dtype=np.float64).reshape(np.shape(xref)[0], -1)
+    num = np.max(np.abs(x - xr), axis=0)
+    den = np.max(np.abs(xr), axis=0)
+    den = np.where(den == 0, 1.0, den)
+    return float(np.max(num / den)) if num.size else 0.0
