@@ -1,0 +1,202 @@
+/*
+ * sptrsv.h - C ABI of a GB300 (sm_103a) sparse lower-triangular solver that
+ * executes forward substitution according to a superstep schedule of the
+ * factor's dependency DAG.
+ *
+ * Method: arXiv:2503.05408, "Efficient parallel scheduling for sparse
+ * triangular solvers".  Citations below name the paper's sections,
+ * equations, definitions and algorithms.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: SPTRSV_OK (0) or a negative
+ *    SPTRSV_ERR_* code.  No exception crosses the ABI and nothing calls
+ *    exit().  sptrsv_status_string() names a code; sptrsv_last_error()
+ *    returns a thread-local message describing the last failure.
+ *  - Host arrays passed in are owned by the caller and only read during the
+ *    call (analyze copies what it needs).
+ *  - Device vectors (b, x) are caller-owned device pointers on the plan's
+ *    device; they must stay valid until the work enqueued on `stream`
+ *    finishes.  Multi-RHS blocks are column-major with leading dimension ld.
+ *  - Opaque handles (sptrsv_plan, sptrsv_batch, sptrsv_server) are owned by
+ *    the library and released by the matching *_destroy call.
+ *  - `stream` is a cudaStream_t passed as an opaque pointer (NULL = the
+ *    legacy default stream).
+ */
+#ifndef SPTRSV_H
+#define SPTRSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef struct CUstream_st *sptrsv_stream;          /* == cudaStream_t */
+typedef struct sptrsv_plan sptrsv_plan;
+
+/* ---------------------------------------------------------------- status */
+enum {
+    SPTRSV_OK = 0,
+    SPTRSV_ERR_ARG = -1,             /* null pointer, bad size, bad option          */
+    SPTRSV_ERR_NOT_LOWER = -2,       /* an entry above the diagonal / out of range  */
+    SPTRSV_ERR_UNSORTED_OR_DUP = -3, /* columns not strictly increasing in a row    */
+    SPTRSV_ERR_ZERO_DIAG = -4,       /* diagonal missing, not last, or zero (Sec. 2.2 assumes
+                                        a non-singular factor)                      */
+    SPTRSV_ERR_OOM = -5,             /* host or device allocation failed            */
+    SPTRSV_ERR_BUDGET = -6,          /* request can never fit the serving budget    */
+    SPTRSV_ERR_CUDA = -7,            /* a CUDA runtime call failed                  */
+    SPTRSV_ERR_LAUNCH = -8,          /* persistent grid cannot be co-resident       */
+    SPTRSV_ERR_TIMEOUT = -9,         /* a bounded device wait expired; x is invalid */
+    SPTRSV_ERR_NOT_CONVERGED = -10,  /* refinement hit max_iters (x still returned) */
+    SPTRSV_ERR_PENDING = -11,        /* serving request not finished yet            */
+    SPTRSV_ERR_NO_DEVICE = -12       /* plan was analysed host-only (device = -1)   */
+};
+
+/* Name of a status code (static string). */
+const char *sptrsv_status_string(int status);
+/* Message of the last failure on the calling thread ("" if none). */
+const char *sptrsv_last_error(void);
+/* Library version as major*10000 + minor*100 + patch. */
+int sptrsv_version(void);
+
+/* ---------------------------------------------------------------- input */
+/* Square lower-triangular factor in CSR, host memory, 0-based, int32 indices.
+ * Each row lists its columns strictly increasing with the diagonal last
+ * (Sec. 2.2: edge (j,i) of the DAG iff A_ij != 0, so the structural entries
+ * define the DAG; the generators never store explicit zeros). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t *rowptr;   /* n + 1 */
+    const int32_t *col;      /* nnz   */
+    const double *val;       /* nnz   */
+} sptrsv_csr;
+
+/* ------------------------------------------------------------- analysis */
+enum {
+    SPTRSV_SCHED_LEVELS = 0,     /* wavefront schedule: superstep = wavefront (Sec. 1) */
+    SPTRSV_SCHED_GROWLOCAL = 1   /* GrowLocal (Sec. 3, Algorithm 3.1)                  */
+};
+enum {                           /* value copies kept on the device (bit mask)        */
+    SPTRSV_VALUES_F64 = 1,       /* FP64 values: plain FP64 solve                     */
+    SPTRSV_VALUES_F32 = 2        /* FP32 hi + FP32 lo split: FP32 sweeps with FP64
+                                    residual refinement, and FP32 solves              */
+};
+
+typedef struct {
+    int32_t mode;      /* SPTRSV_SCHED_*                                                  */
+    int32_t k;         /* GrowLocal cores; 0 = number of SMs of `device` (1 if host-only)  */
+    double alpha0;     /* first superstep length (20, Sec. 3)                              */
+    double growth;     /* alpha growth per attempt (1.5, Sec. 3)                           */
+    double L;          /* barrier cost in Eq. 3.1 (500, Sec. 3 footnote)                   */
+    double accept;     /* worthy iff beta >= accept * best beta (0.97, App. B)             */
+    int32_t values;    /* SPTRSV_VALUES_* mask; 0 = F64 | F32                              */
+    int32_t device;    /* CUDA device ordinal, or -1: analyse on the host only (no upload;
+                          sptrsv_solve then returns SPTRSV_ERR_NO_DEVICE)                  */
+} sptrsv_analyze_opts;
+
+/* Fill `o` with the defaults above (LEVELS, k = 0, 20, 1.5, 500, 0.97, both value
+ * copies, device 0). */
+void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o);
+
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int32_t levels;          /* number of wavefronts = longest path in vertices (Sec. 6.2) */
+    int32_t supersteps;      /* S of the chosen schedule                                   */
+    int32_t k;               /* cores of the schedule (1 for LEVELS)                       */
+    int32_t max_level_rows;  /* widest wavefront                                           */
+    double avg_wavefront;    /* n / levels (Sec. 6.2)                                      */
+    int64_t device_bytes;    /* bytes resident on the device for this plan                 */
+    double analyze_ms;       /* host wall time of sptrsv_analyze                           */
+} sptrsv_stats;
+
+/* Analyse a factor (Sec. 2.2 DAG, Sec. 1 wavefronts, Sec. 3 schedule, Sec. 5
+ * reordering) and, unless opts->device == -1, upload a superstep-contiguous
+ * copy to the device.
+ *   csr   : host CSR, validated (errors NOT_LOWER, UNSORTED_OR_DUP, ZERO_DIAG, ARG).
+ *   opts  : may be NULL for the defaults.
+ *   out   : receives the plan; NULL on error.
+ * The call is synchronous; it owns no caller memory afterwards. */
+int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out);
+
+/* Statistics of an analysed plan. */
+int sptrsv_plan_stats(const sptrsv_plan *plan, sptrsv_stats *out);
+
+/* Copy the schedule to caller host buffers of n int32 each (any may be NULL):
+ *   level[v] : wavefront of row v (0-based)
+ *   sigma[v] : superstep of row v (0-based; Def. 2.1 sigma minus one)
+ *   pi[v]    : core of row v (0-based; Def. 2.1 pi minus one)
+ *   perm[r]  : original row at position r of the Sec. 5 reordering
+ *              (sorted by superstep, then core, then original id). */
+int sptrsv_plan_export(const sptrsv_plan *plan, int32_t *level, int32_t *sigma, int32_t *pi,
+                       int32_t *perm);
+
+/* Release a plan and its device memory (NULL is a no-op).  The caller must
+ * ensure no enqueued solve still uses it. */
+void sptrsv_destroy(sptrsv_plan *plan);
+
+/* ---------------------------------------------------------------- solve */
+enum { SPTRSV_F64 = 0, SPTRSV_F32 = 1 };             /* dtype of b and x */
+enum {
+    SPTRSV_SYNC_AUTO = 0,   /* autotuned per plan                                          */
+    SPTRSV_SYNC_GRID = 1,   /* persistent grid, one grid-wide barrier per superstep         */
+    SPTRSV_SYNC_FLAGS = 2,  /* persistent grid, per-row ready flags on cross-CTA parents    */
+    SPTRSV_SYNC_CTA = 3     /* one thread block walks all supersteps (small factors)        */
+};
+enum {
+    SPTRSV_PREC_F64 = 0,         /* FP64 values and arithmetic (needs SPTRSV_VALUES_F64)    */
+    SPTRSV_PREC_F32_REFINE = 1   /* FP32 sweeps + FP64 residual r = b - Lx and FP64 update
+                                    x += d, repeated until converged (needs VALUES_F32)     */
+};
+
+typedef struct {
+    int32_t sync;        /* SPTRSV_SYNC_*                                                    */
+    int32_t lanes;       /* lanes per row: 0 = auto, or 1, 2, 4, 8, 16, 32                   */
+    int32_t precision;   /* SPTRSV_PREC_* for dtype F64 (dtype F32 always solves in FP32)    */
+    int32_t max_iters;   /* refinement: maximum correction sweeps after the first (6)        */
+    double refine_tol;   /* refinement stops when ||d||inf <= refine_tol * ||x||inf (1e-14)   */
+    int32_t blocks_per_sm; /* persistent grid size per SM; 0 = auto                          */
+    int32_t threads;     /* threads per block; 0 = auto                                      */
+    double timeout_s;    /* limit of every bounded device wait, seconds (default 2.0)         */
+} sptrsv_solve_opts;
+
+void sptrsv_solve_opts_default(sptrsv_solve_opts *o);
+
+typedef struct {
+    int32_t status;        /* SPTRSV_OK, ERR_TIMEOUT or ERR_NOT_CONVERGED                     */
+    int32_t sweeps;        /* dependent sweeps run (1 for a plain solve)                      */
+    int64_t barriers;      /* grid-wide barriers executed (device counter)                    */
+    int64_t flag_waits;    /* cross-CTA ready-flag waits that had to spin (device counter)    */
+    double dnorm;          /* refinement: last ||d||inf / ||x||inf (0 for a plain solve)      */
+    int32_t sync;          /* sync mode actually used                                         */
+    int32_t lanes;         /* lanes per row actually used                                     */
+    int32_t grid;          /* thread blocks launched                                          */
+    int32_t threads;       /* threads per block                                               */
+} sptrsv_report;
+
+/* Solve L X = B for nrhs right-hand sides (Eq. 2.1 in the plan's schedule).
+ *   b, x   : device pointers, column-major n x nrhs, leading dimension ld >= n; b is
+ *            read only, x receives the solution in ORIGINAL row order.  b and x
+ *            must not overlap.  dtype SPTRSV_F64 (double) or SPTRSV_F32 (float).
+ *   opts   : may be NULL for defaults.
+ *   stream : enqueue on this stream.
+ *   report : NULL -> fully asynchronous (device errors surface on the next call
+ *            with a report); non-NULL -> the call synchronises `stream` and fills it.
+ * Errors: ARG (sizes, dtype/precision without the needed value copy), NO_DEVICE,
+ * LAUNCH (grid not co-resident), CUDA, TIMEOUT, NOT_CONVERGED (x still written). */
+int sptrsv_solve(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_t ld,
+                 int32_t dtype, const sptrsv_solve_opts *opts, sptrsv_stream stream,
+                 sptrsv_report *report);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPTRSV_H */

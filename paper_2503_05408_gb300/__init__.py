@@ -1,0 +1,244 @@
+"""Thin Python binding of ``libsptrsv.so`` (the C ABI declared in include/sptrsv.h).
+
+Argument marshalling only: every step of the solve runs in the library's own
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback - if the in-tree library has not been built the import of this
+module succeeds but every call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsptrsv.so")
+
+# ---------------------------------------------------------------- constants
+OK = 0
+ERR_ARG, ERR_NOT_LOWER, ERR_UNSORTED_OR_DUP, ERR_ZERO_DIAG = -1, -2, -3, -4
+ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT = -5, -6, -7, -8, -9
+ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE = -10, -11, -12
+
+SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
+VALUES_F64, VALUES_F32 = 1, 2
+F64, F32 = 0, 1
+SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA = 0, 1, 2, 3
+PREC_F64, PREC_F32_REFINE = 0, 1
+
+SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta"}
+_SYNC = {"auto": SYNC_AUTO, "grid": SYNC_GRID, "flags": SYNC_FLAGS, "cta": SYNC_CTA}
+_MODE = {"levels": SCHED_LEVELS, "growlocal": SCHED_GROWLOCAL}
+_PREC = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}
+
+
+class SptrsvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+# ---------------------------------------------------------------- structs
+class CSRStruct(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class AnalyzeOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha0", ctypes.c_double),
+                ("growth", ctypes.c_double), ("L", ctypes.c_double), ("accept", ctypes.c_double),
+                ("values", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("supersteps", ctypes.c_int32), ("k", ctypes.c_int32), ("max_level_rows", ctypes.c_int32),
+                ("avg_wavefront", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("analyze_ms", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("sync", ctypes.c_int32), ("lanes", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double),
+                ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("timeout_s", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("barriers", ctypes.c_int64),
+                ("flag_waits", ctypes.c_int64), ("dnorm", ctypes.c_double), ("sync", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["sync_name"] = SYNC_NAMES.get(self.sync, str(self.sync))
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree library; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "sptrsv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "sptrsv_last_error": (ctypes.c_char_p, []),
+            "sptrsv_version": (ctypes.c_int, []),
+            "sptrsv_analyze_opts_default": (None, [ctypes.POINTER(AnalyzeOpts)]),
+            "sptrsv_analyze": (ctypes.c_int, [ctypes.POINTER(CSRStruct), ctypes.POINTER(AnalyzeOpts),
+                                              ctypes.POINTER(vp)]),
+            "sptrsv_plan_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+            "sptrsv_plan_export": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "sptrsv_destroy": (None, [vp]),
+            "sptrsv_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+            "sptrsv_solve": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
+                                            ctypes.POINTER(Report)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        L = lib()
+        raise SptrsvError(status, f"{L.sptrsv_status_string(status).decode()}: "
+                                  f"{L.sptrsv_last_error().decode()}")
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().sptrsv_solve_opts_default(ctypes.byref(o))
+    for key, v in kw.items():
+        if v is None:
+            continue
+        if key == "sync" and isinstance(v, str):
+            v = _SYNC[v]
+        if key == "precision" and isinstance(v, str):
+            v = _PREC[v]
+        setattr(o, key, v)
+    return o
+
+
+@dataclass
+class ScheduleExport:
+    level: np.ndarray
+    sigma: np.ndarray
+    pi: np.ndarray
+    perm: np.ndarray
+
+
+class Plan:
+    """An analysed factor: ``Plan(A)`` with ``A`` having ``n, rowptr, col, val`` (numpy)."""
+
+    def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
+                 values=VALUES_F64 | VALUES_F32, device=0):
+        lb = lib()
+        self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        self._col = np.ascontiguousarray(A.col, dtype=np.int32)
+        self._val = np.ascontiguousarray(A.val, dtype=np.float64)
+        if self._rowptr.size != int(A.n) + 1 or self._val.size != self._col.size:
+            raise ValueError("rowptr must have n + 1 entries and val as many as col")
+        csr = CSRStruct(int(A.n), int(self._col.size), _ptr(self._rowptr),
+                        _ptr(self._col), _ptr(self._val))
+        o = AnalyzeOpts()
+        lb.sptrsv_analyze_opts_default(ctypes.byref(o))
+        o.mode = _MODE[mode] if isinstance(mode, str) else int(mode)
+        o.k, o.alpha0, o.growth, o.L, o.accept = int(k), alpha0, growth, L, accept
+        o.values, o.device = int(values), int(device)
+        h = ctypes.c_void_p()
+        self.handle = None
+        _check(lb.sptrsv_analyze(ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self.n = int(A.n)
+        self.device = int(device)
+        del self._rowptr, self._col, self._val       # analyze copied what it needs
+
+    def close(self):
+        if self.handle:
+            lib().sptrsv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().sptrsv_plan_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def export(self) -> ScheduleExport:
+        arrs = [np.empty(self.n, dtype=np.int32) for _ in range(4)]
+        _check(lib().sptrsv_plan_export(self.handle, *[_ptr(a) for a in arrs]))
+        return ScheduleExport(*arrs)
+
+    def solve(self, b, x=None, *, stream=None, report=True, **opts):
+        """Solve L x = b for a CUDA tensor ``b`` of shape (n,) or (n, nrhs) column-major
+        (stride (1, ld)); ``x`` is allocated like ``b`` if not given.  Returns (x, report)."""
+        import torch
+        if not (isinstance(b, torch.Tensor) and b.is_cuda):
+            raise TypeError("b must be a CUDA tensor")
+        if b.dtype == torch.float64:
+            dtype = F64
+        elif b.dtype == torch.float32:
+            dtype = F32
+        else:
+            raise TypeError("b must be float64 or float32")
+        if b.dim() == 1:
+            nrhs, ld = 1, max(self.n, 1)
+            if b.stride(0) != 1:
+                raise ValueError("b must be contiguous")
+        elif b.dim() == 2:
+            nrhs = b.shape[1]
+            if b.stride(0) != 1:
+                raise ValueError("b must be column-major: stride (1, ld)")
+            ld = b.stride(1) if nrhs > 1 else max(self.n, 1)
+        else:
+            raise ValueError("b must be 1-D or 2-D")
+        if b.shape[0] != self.n:
+            raise ValueError("b has the wrong number of rows")
+        if x is None:
+            x = torch.empty_strided(b.shape, b.stride(), dtype=b.dtype, device=b.device)
+        if x.dtype != b.dtype or x.shape != b.shape or x.stride() != b.stride():
+            raise ValueError("x must match b in dtype, shape and strides")
+        rep = Report()
+        o = solve_opts(**opts)
+        st = lib().sptrsv_solve(self.handle, _ptr(b), _ptr(x), int(nrhs), int(ld), dtype,
+                                ctypes.byref(o), _stream_handle(stream),
+                                ctypes.byref(rep) if report else None)
+        _check(st)
+        return x, (rep.as_dict() if report else None)

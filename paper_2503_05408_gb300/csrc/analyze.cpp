@@ -1,0 +1,305 @@
+// Host analysis: input validation, the DAG of Sec. 2.2, wavefronts (Sec. 1),
+// the superstep schedule (wavefronts or GrowLocal, Sec. 3), the Sec. 5
+// reordering and the execution structure the device kernels walk.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace sptrsv {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int fail(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+void clear_error() { g_last_error.clear(); }
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+// Input rules (Sec. 2.2 assumes a non-singular lower-triangular factor):
+// row pointers monotone from 0 to nnz, columns in [0, row], strictly
+// increasing, the diagonal present, last and non-zero.
+int validate_csr(const sptrsv_csr *A) {
+    if (!A) return fail(SPTRSV_ERR_ARG, "csr is NULL");
+    if (A->n < 0 || A->nnz < 0) return fail(SPTRSV_ERR_ARG, "negative size");
+    if (A->n > 0 && (!A->rowptr || !A->col || !A->val))
+        return fail(SPTRSV_ERR_ARG, "csr array is NULL");
+    if (A->nnz > INT32_MAX) return fail(SPTRSV_ERR_ARG, "nnz exceeds int32 indexing");
+    if (A->n == 0) return SPTRSV_OK;
+    if (A->rowptr[0] != 0 || int64_t(A->rowptr[A->n]) != A->nnz)
+        return fail(SPTRSV_ERR_ARG, "rowptr[0] must be 0 and rowptr[n] must equal nnz");
+    for (int32_t i = 0; i < A->n; ++i) {
+        const int32_t lo = A->rowptr[i], hi = A->rowptr[i + 1];
+        if (hi < lo) return fail(SPTRSV_ERR_ARG, "rowptr decreases at row " + std::to_string(i));
+        if (hi == lo) return fail(SPTRSV_ERR_ZERO_DIAG, "row " + std::to_string(i) + " is empty");
+        for (int32_t q = lo; q < hi; ++q) {
+            const int32_t c = A->col[q];
+            if (c < 0 || c > i)
+                return fail(SPTRSV_ERR_NOT_LOWER, "entry (" + std::to_string(i) + "," +
+                                                      std::to_string(c) + ") outside the lower triangle");
+            if (q > lo && c <= A->col[q - 1])
+                return fail(SPTRSV_ERR_UNSORTED_OR_DUP,
+                            "columns of row " + std::to_string(i) + " not strictly increasing");
+        }
+        if (A->col[hi - 1] != i)
+            return fail(SPTRSV_ERR_ZERO_DIAG, "diagonal of row " + std::to_string(i) + " missing");
+        if (A->val[hi - 1] == 0.0)
+            return fail(SPTRSV_ERR_ZERO_DIAG, "zero diagonal in row " + std::to_string(i));
+    }
+    return SPTRSV_OK;
+}
+
+namespace {
+
+// Wavefront of every row: 0 without parents, else 1 + deepest parent.  The
+// natural order of a lower-triangular factor is topological.
+int32_t compute_levels(const sptrsv_csr *A, std::vector<int32_t> &level) {
+    level.assign(A->n, 0);
+    int32_t deepest = -1;
+    for (int32_t i = 0; i < A->n; ++i) {
+        int32_t d = 0;
+        const int32_t last = A->rowptr[i + 1] - 1;
+        for (int32_t q = A->rowptr[i]; q < last; ++q) d = std::max(d, level[A->col[q]] + 1);
+        level[i] = d;
+        deepest = std::max(deepest, d);
+    }
+    return deepest + 1;
+}
+
+// Stable counting sort of `ids` by key[id] in [0, nkeys).
+void stable_bucket(std::vector<int32_t> &ids, const std::vector<int32_t> &key, int32_t nkeys) {
+    std::vector<int64_t> start(size_t(nkeys) + 1, 0);
+    for (int32_t v : ids) start[size_t(key[v]) + 1]++;
+    for (int32_t b = 0; b < nkeys; ++b) start[b + 1] += start[b];
+    std::vector<int32_t> out(ids.size());
+    for (int32_t v : ids) out[start[key[v]]++] = v;
+    ids.swap(out);
+}
+
+}  // namespace
+
+int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h) {
+    const int32_t n = A->n;
+    h.n = n;
+    h.nnz = A->nnz;
+    h.mode = o.mode;
+    h.nlevels = n ? compute_levels(A, h.level) : 0;
+    {
+        std::vector<int32_t> width(size_t(h.nlevels), 0);
+        for (int32_t v = 0; v < n; ++v) width[h.level[v]]++;
+        h.max_level_rows = width.empty() ? 0 : *std::max_element(width.begin(), width.end());
+    }
+    h.sigma.assign(n, 0);
+    h.pi.assign(n, 0);
+    if (o.mode == SPTRSV_SCHED_LEVELS) {
+        h.k = 1;
+        h.sigma = h.level;
+        h.S = h.nlevels;
+    } else if (o.mode == SPTRSV_SCHED_GROWLOCAL) {
+        h.k = o.k;
+        h.S = growlocal_schedule(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept,
+                                 h.sigma.data(), h.pi.data());
+    } else {
+        return fail(SPTRSV_ERR_ARG, "unknown schedule mode");
+    }
+
+    // Sec. 5: order by superstep, then core, then original id (LSD: core, then superstep).
+    h.perm.resize(n);
+    for (int32_t v = 0; v < n; ++v) h.perm[v] = v;
+    stable_bucket(h.perm, h.pi, h.k);
+    stable_bucket(h.perm, h.sigma, std::max(h.S, 1));
+
+    // Phases inside a (superstep, core) block: depth among same-block parents.
+    // Rows are visited in original order, which is topological.
+    std::vector<int32_t> sub(n, 0);
+    int32_t max_sub = 0;
+    if (o.mode != SPTRSV_SCHED_LEVELS) {
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t d = 0;
+            const int32_t last = A->rowptr[v + 1] - 1;
+            for (int32_t q = A->rowptr[v]; q < last; ++q) {
+                const int32_t u = A->col[q];
+                if (h.sigma[u] == h.sigma[v] && h.pi[u] == h.pi[v]) d = std::max(d, sub[u] + 1);
+            }
+            sub[v] = d;
+            max_sub = std::max(max_sub, d);
+        }
+    }
+    // Device order: the Sec. 5 order refined by phase inside each block.
+    h.dev_perm = h.perm;
+    if (max_sub > 0) {
+        size_t a = 0;
+        std::vector<int32_t> tmp;
+        while (a < size_t(n)) {
+            size_t b = a;
+            const int32_t s = h.sigma[h.dev_perm[a]], p = h.pi[h.dev_perm[a]];
+            while (b < size_t(n) && h.sigma[h.dev_perm[b]] == s && h.pi[h.dev_perm[b]] == p) ++b;
+            std::stable_sort(h.dev_perm.begin() + a, h.dev_perm.begin() + b,
+                             [&](int32_t x, int32_t y) { return sub[x] < sub[y]; });
+            a = b;
+        }
+    }
+    // Walk the device order and cut supersteps, blocks and phases.
+    h.step_blk.assign(1, 0);
+    h.blk_phase.assign(1, 0);
+    h.phase_row.assign(1, 0);
+    h.max_phase_rows = 0;
+    h.max_block_rows = 0;
+    int32_t r = 0;
+    while (r < n) {
+        const int32_t s = h.sigma[h.dev_perm[r]];
+        while (r < n && h.sigma[h.dev_perm[r]] == s) {            // blocks of superstep s
+            const int32_t p = h.pi[h.dev_perm[r]];
+            const int32_t blk_start = r;
+            while (r < n && h.sigma[h.dev_perm[r]] == s && h.pi[h.dev_perm[r]] == p) {
+                const int32_t d = sub[h.dev_perm[r]];
+                const int32_t ph_start = r;
+                while (r < n && h.sigma[h.dev_perm[r]] == s && h.pi[h.dev_perm[r]] == p &&
+                       sub[h.dev_perm[r]] == d)
+                    ++r;
+                h.phase_row.push_back(r);
+                h.max_phase_rows = std::max(h.max_phase_rows, r - ph_start);
+            }
+            h.blk_phase.push_back(int32_t(h.phase_row.size()) - 1);
+            h.max_block_rows = std::max(h.max_block_rows, r - blk_start);
+        }
+        h.step_blk.push_back(int32_t(h.blk_phase.size()) - 1);
+    }
+    if (int32_t(h.step_blk.size()) - 1 != h.S)
+        return fail(SPTRSV_ERR_ARG, "internal: superstep count mismatch");
+    return SPTRSV_OK;
+}
+
+}  // namespace sptrsv
+
+using namespace sptrsv;
+
+extern "C" {
+
+const char *sptrsv_status_string(int status) {
+    switch (status) {
+        case SPTRSV_OK: return "SPTRSV_OK";
+        case SPTRSV_ERR_ARG: return "SPTRSV_ERR_ARG";
+        case SPTRSV_ERR_NOT_LOWER: return "SPTRSV_ERR_NOT_LOWER";
+        case SPTRSV_ERR_UNSORTED_OR_DUP: return "SPTRSV_ERR_UNSORTED_OR_DUP";
+        case SPTRSV_ERR_ZERO_DIAG: return "SPTRSV_ERR_ZERO_DIAG";
+        case SPTRSV_ERR_OOM: return "SPTRSV_ERR_OOM";
+        case SPTRSV_ERR_BUDGET: return "SPTRSV_ERR_BUDGET";
+        case SPTRSV_ERR_CUDA: return "SPTRSV_ERR_CUDA";
+        case SPTRSV_ERR_LAUNCH: return "SPTRSV_ERR_LAUNCH";
+        case SPTRSV_ERR_TIMEOUT: return "SPTRSV_ERR_TIMEOUT";
+        case SPTRSV_ERR_NOT_CONVERGED: return "SPTRSV_ERR_NOT_CONVERGED";
+        case SPTRSV_ERR_PENDING: return "SPTRSV_ERR_PENDING";
+        case SPTRSV_ERR_NO_DEVICE: return "SPTRSV_ERR_NO_DEVICE";
+        default: return "SPTRSV_ERR_UNKNOWN";
+    }
+}
+
+const char *sptrsv_last_error(void) { return last_error_cstr(); }
+
+int sptrsv_version(void) { return 10000; }
+
+void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o) {
+    if (!o) return;
+    o->mode = SPTRSV_SCHED_LEVELS;
+    o->k = 0;
+    o->alpha0 = 20.0;
+    o->growth = 1.5;
+    o->L = 500.0;
+    o->accept = 0.97;
+    o->values = SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32;
+    o->device = 0;
+}
+
+int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out) {
+    clear_error();
+    if (!out) return fail(SPTRSV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    sptrsv_analyze_opts o;
+    sptrsv_analyze_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.values == 0) o.values = SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32;
+    if (o.values & ~(SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "bad values mask");
+    if (o.device < -1) return fail(SPTRSV_ERR_ARG, "bad device");
+    if (o.mode == SPTRSV_SCHED_GROWLOCAL) {
+        if (!(o.alpha0 >= 1.0) || !(o.growth > 1.0) || !(o.L >= 0.0) || !(o.accept > 0.0))
+            return fail(SPTRSV_ERR_ARG, "GrowLocal needs alpha0 >= 1, growth > 1, L >= 0, accept > 0");
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    int st = validate_csr(csr);
+    if (st) return st;
+    int32_t sms = 1;
+    if (o.device >= 0) {
+        st = device_sm_count(o.device, &sms);
+        if (st) return st;
+    }
+    if (o.mode == SPTRSV_SCHED_GROWLOCAL && o.k <= 0) o.k = sms;
+    if (o.mode == SPTRSV_SCHED_GROWLOCAL && o.k > (1 << 20)) return fail(SPTRSV_ERR_ARG, "k too large");
+
+    sptrsv_plan *p = new (std::nothrow) sptrsv_plan();
+    if (!p) return fail(SPTRSV_ERR_OOM, "host allocation failed");
+    try {
+        st = build_schedule(csr, o, p->h);
+    } catch (const std::bad_alloc &) {
+        st = fail(SPTRSV_ERR_OOM, "host allocation failed during analysis");
+    }
+    if (st) {
+        delete p;
+        return st;
+    }
+    p->values = o.values;
+    p->device = o.device;
+    p->num_sms = sms;
+    p->nnz_off = csr->nnz - csr->n;
+    if (o.device >= 0) {
+        st = upload_plan(p, csr);
+        if (st) {
+            free_device(p);
+            delete p;
+            return st;
+        }
+    }
+    p->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return SPTRSV_OK;
+}
+
+int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
+    if (!p || !out) return fail(SPTRSV_ERR_ARG, "NULL argument");
+    out->n = p->h.n;
+    out->nnz = p->h.nnz;
+    out->levels = p->h.nlevels;
+    out->supersteps = p->h.S;
+    out->k = p->h.k;
+    out->max_level_rows = p->h.max_level_rows;
+    out->avg_wavefront = p->h.nlevels ? double(p->h.n) / p->h.nlevels : 0.0;
+    out->device_bytes = p->device_bytes;
+    out->analyze_ms = p->analyze_ms;
+    return SPTRSV_OK;
+}
+
+int sptrsv_plan_export(const sptrsv_plan *p, int32_t *level, int32_t *sigma, int32_t *pi, int32_t *perm) {
+    if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
+    const size_t bytes = size_t(p->h.n) * sizeof(int32_t);
+    if (level && bytes) std::memcpy(level, p->h.level.data(), bytes);
+    if (sigma && bytes) std::memcpy(sigma, p->h.sigma.data(), bytes);
+    if (pi && bytes) std::memcpy(pi, p->h.pi.data(), bytes);
+    if (perm && bytes) std::memcpy(perm, p->h.perm.data(), bytes);
+    return SPTRSV_OK;
+}
+
+void sptrsv_destroy(sptrsv_plan *p) {
+    if (!p) return;
+    free_device(p);
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,348 @@
+// Device residency of a plan and the single-factor solve entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.hpp"
+
+namespace sptrsv {
+
+#define CUDA_TRY(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA, \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+int device_sm_count(int device, int32_t *out) {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device >= count)
+        return fail(SPTRSV_ERR_CUDA, std::string("no CUDA device ") + std::to_string(device) + ": " +
+                                         cudaGetErrorString(e));
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    *out = sms;
+    return SPTRSV_OK;
+}
+
+namespace {
+
+template <typename T>
+int upload(const std::vector<T> &h, T **d, int64_t *bytes) {
+    const size_t nb = std::max<size_t>(h.size(), 1) * sizeof(T);
+    CUDA_TRY(cudaMalloc((void **)d, nb));
+    if (!h.empty()) CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *bytes += int64_t(nb);
+    return SPTRSV_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
+    DeviceGuard g(p->device);
+    const HostSchedule &h = p->h;
+    const int32_t n = h.n;
+    // gather the factor in device order, off-diagonals and diagonal apart
+    std::vector<int32_t> rp(size_t(n) + 1, 0), col;
+    std::vector<double> val, diag(n);
+    col.reserve(size_t(p->nnz_off));
+    val.reserve(size_t(p->nnz_off));
+    for (int32_t r = 0; r < n; ++r) {
+        const int32_t v = h.dev_perm[r];
+        const int32_t lo = A->rowptr[v], last = A->rowptr[v + 1] - 1;
+        for (int32_t q = lo; q < last; ++q) {
+            col.push_back(A->col[q]);
+            val.push_back(A->val[q]);
+        }
+        diag[r] = A->val[last];
+        rp[r + 1] = int32_t(col.size());
+    }
+    int64_t bytes = 0;
+    int st;
+    DeviceBuffers &d = p->d;
+    if ((st = upload(rp, &d.rp, &bytes))) return st;
+    if ((st = upload(col, &d.col, &bytes))) return st;
+    if (p->values & SPTRSV_VALUES_F64) {
+        if ((st = upload(val, &d.val, &bytes))) return st;
+        if ((st = upload(diag, &d.diag, &bytes))) return st;
+    }
+    if (p->values & SPTRSV_VALUES_F32) {
+        // hi = fp32(v), lo = fp32(v - hi): hi + lo carries ~48 bits of v for the
+        // FP64 residual, hi alone drives the FP32 sweeps.
+        std::vector<float> hi(val.size()), lo(val.size()), dhi(n), dlo(n);
+        for (size_t i = 0; i < val.size(); ++i) {
+            hi[i] = float(val[i]);
+            lo[i] = float(val[i] - double(hi[i]));
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            dhi[i] = float(diag[i]);
+            dlo[i] = float(diag[i] - double(dhi[i]));
+        }
+        if ((st = upload(hi, &d.val_hi, &bytes))) return st;
+        if ((st = upload(lo, &d.val_lo, &bytes))) return st;
+        if ((st = upload(dhi, &d.diag_hi, &bytes))) return st;
+        if ((st = upload(dlo, &d.diag_lo, &bytes))) return st;
+    }
+    if ((st = upload(h.dev_perm, &d.perm, &bytes))) return st;
+    if ((st = upload(h.step_blk, &d.step_blk, &bytes))) return st;
+    if ((st = upload(h.blk_phase, &d.blk_phase, &bytes))) return st;
+    if ((st = upload(h.phase_row, &d.phase_row, &bytes))) return st;
+    CUDA_TRY(cudaMalloc((void **)&d.counters, sizeof(Ctl)));
+    CUDA_TRY(cudaMemset(d.counters, 0, sizeof(Ctl)));
+    bytes += sizeof(Ctl);
+    CUDA_TRY(cudaMalloc((void **)&d.flags, std::max<size_t>(size_t(n), 1) * sizeof(uint32_t)));
+    CUDA_TRY(cudaMemset(d.flags, 0, std::max<size_t>(size_t(n), 1) * sizeof(uint32_t)));
+    bytes += int64_t(std::max<size_t>(size_t(n), 1) * sizeof(uint32_t));
+    p->device_bytes = bytes;
+    return SPTRSV_OK;
+}
+
+void free_device(sptrsv_plan *p) {
+    if (!p || p->device < 0) return;
+    DeviceGuard g(p->device);
+    DeviceBuffers &d = p->d;
+    void *ptrs[] = {d.rp,       d.col,      d.val,       d.diag,     d.val_hi, d.val_lo, d.diag_hi,
+                    d.diag_lo,  d.perm,     d.step_blk,  d.blk_phase, d.phase_row, d.counters,
+                    d.flags,    d.work};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    d = DeviceBuffers();
+}
+
+// ------------------------------------------------------------------ launch
+namespace {
+
+template <typename T>
+using Kern = void (*)(SolveArgs<T>);
+
+template <typename T>
+Kern<T> pick_kernel(int sync, int lanes) {
+#define SPTRSV_LANES_CASE(L)                                          \
+    case L:                                                           \
+        return sync == SPTRSV_SYNC_GRID    ? k_grid<T, L>             \
+               : sync == SPTRSV_SYNC_FLAGS ? k_flags<T, L>            \
+                                           : k_cta<T, L>;
+    switch (lanes) {
+        SPTRSV_LANES_CASE(1)
+        SPTRSV_LANES_CASE(2)
+        SPTRSV_LANES_CASE(4)
+        SPTRSV_LANES_CASE(8)
+        SPTRSV_LANES_CASE(16)
+        SPTRSV_LANES_CASE(32)
+        default: return nullptr;
+    }
+#undef SPTRSV_LANES_CASE
+}
+
+struct LaunchCfg {
+    int sync, lanes, threads, grid;
+};
+
+int auto_lanes(const sptrsv_plan *p) {
+    const double per_row = p->h.n ? double(p->nnz_off) / p->h.n : 0.0;
+    if (per_row <= 4.0) return 1;
+    if (per_row <= 12.0) return 4;
+    if (per_row <= 32.0) return 8;
+    return 32;
+}
+
+template <typename T>
+int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o, LaunchCfg &c) {
+    c.sync = o.sync;
+    if (c.sync == SPTRSV_SYNC_AUTO) {
+        if (p->h.n <= 8192) c.sync = SPTRSV_SYNC_CTA;
+        else if (p->h.mode == SPTRSV_SCHED_LEVELS) c.sync = SPTRSV_SYNC_FLAGS;
+        else c.sync = SPTRSV_SYNC_GRID;
+    }
+    c.lanes = o.lanes ? o.lanes : auto_lanes(p);
+    if (!pick_kernel<T>(c.sync, c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8, 16 or 32");
+    c.threads = o.threads ? o.threads : (c.sync == SPTRSV_SYNC_CTA ? 1024 : 256);
+    if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
+        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+    if (c.sync == SPTRSV_SYNC_CTA) {
+        c.grid = 1;
+        return SPTRSV_OK;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel<T>(c.sync, c.lanes),
+                                                                  c.threads, 0);
+    if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, cudaGetErrorString(e));
+    int want = o.blocks_per_sm ? o.blocks_per_sm : std::min(per_sm, c.sync == SPTRSV_SYNC_GRID ? 1 : 4);
+    if (want > per_sm)
+        return fail(SPTRSV_ERR_LAUNCH, "persistent grid of " + std::to_string(want) +
+                                           " blocks/SM cannot be co-resident (max " +
+                                           std::to_string(per_sm) + ")");
+    c.grid = std::max(1, want * p->num_sms);
+    return SPTRSV_OK;
+}
+
+template <typename T>
+int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStream_t s) {
+    Kern<T> k = pick_kernel<T>(c.sync, c.lanes);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.grid);
+    cfg.blockDim = dim3(c.threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = (c.sync == SPTRSV_SYNC_CTA) ? 0 : 1;   // co-residency guaranteed or error
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, args);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(e == cudaErrorCooperativeLaunchTooLarge ? SPTRSV_ERR_LAUNCH : SPTRSV_ERR_CUDA,
+                    std::string("launch: ") + cudaGetErrorString(e));
+    }
+    return SPTRSV_OK;
+}
+
+template <typename T>
+SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *diag) {
+    SolveArgs<T> a;
+    a.n = p->h.n;
+    a.S = p->h.S;
+    a.nrhs = 0;
+    a.rp = p->d.rp;
+    a.col = p->d.col;
+    a.val = val;
+    a.diag = diag;
+    a.perm = p->d.perm;
+    a.step_blk = p->d.step_blk;
+    a.blk_phase = p->d.blk_phase;
+    a.phase_row = p->d.phase_row;
+    a.b = nullptr;
+    a.x = nullptr;
+    a.ldb = a.ldx = 0;
+    a.ctl = reinterpret_cast<Ctl *>(p->d.counters);
+    a.flags = p->d.flags;
+    a.epoch = 0;
+    a.timeout_ns = 0;
+    return a;
+}
+
+uint32_t next_epoch(sptrsv_plan *p, cudaStream_t s) {
+    if (++p->epoch == 0) {                      // wrapped: clear the flags once
+        cudaMemsetAsync(p->d.flags, 0, std::max<size_t>(size_t(p->h.n), 1) * sizeof(uint32_t), s);
+        p->epoch = 1;
+    }
+    return p->epoch;
+}
+
+template <typename T>
+int plain_solve(sptrsv_plan *p, const T *val, const T *diag, const void *b, void *x, int32_t nrhs, int64_t ld,
+                const sptrsv_solve_opts &o, cudaStream_t s, LaunchCfg &c) {
+    int st = choose<T>(p, o, c);
+    if (st) return st;
+    SolveArgs<T> a = base_args<T>(p, val, diag);
+    a.nrhs = nrhs;
+    a.b = static_cast<const T *>(b);
+    a.x = static_cast<T *>(x);
+    a.ldb = a.ldx = ld;
+    a.timeout_ns = (long long)(o.timeout_s * 1e9);
+    if (c.sync == SPTRSV_SYNC_FLAGS) a.epoch = next_epoch(p, s);
+    // zero the counters but keep the status word: a device error of an
+    // asynchronous solve stays visible until a report reads and clears it
+    CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
+    return launch<T>(p, c, a, s);
+}
+
+}  // namespace
+}  // namespace sptrsv
+
+using namespace sptrsv;
+
+extern "C" {
+
+void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
+    if (!o) return;
+    o->sync = SPTRSV_SYNC_AUTO;
+    o->lanes = 0;
+    o->precision = SPTRSV_PREC_F64;
+    o->max_iters = 6;
+    o->refine_tol = 1e-14;
+    o->blocks_per_sm = 0;
+    o->threads = 0;
+    o->timeout_s = 2.0;
+}
+
+int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
+                 const sptrsv_solve_opts *opts, sptrsv_stream stream, sptrsv_report *report) {
+    clear_error();
+    if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SPTRSV_ERR_NO_DEVICE, "plan was analysed host-only");
+    sptrsv_solve_opts o;
+    sptrsv_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (nrhs < 0 || (p->h.n > 0 && nrhs > 0 && (!b || !x)) || ld < std::max<int64_t>(p->h.n, 1))
+        return fail(SPTRSV_ERR_ARG, "bad b/x/nrhs/ld");
+    if (!(o.timeout_s > 0.0)) return fail(SPTRSV_ERR_ARG, "timeout_s must be positive");
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    LaunchCfg c{};
+    int st = SPTRSV_OK;
+    if (p->h.n == 0 || nrhs == 0) {
+        if (report) {
+            std::memset(report, 0, sizeof(*report));
+        }
+        return SPTRSV_OK;
+    }
+    if (dtype == SPTRSV_F64) {
+        if (o.precision == SPTRSV_PREC_F64) {
+            if (!(p->values & SPTRSV_VALUES_F64)) return fail(SPTRSV_ERR_ARG, "plan has no FP64 values");
+            st = plain_solve<double>(p, p->d.val, p->d.diag, b, x, nrhs, ld, o, s, c);
+        } else {
+            return fail(SPTRSV_ERR_ARG, "precision mode not available yet");
+        }
+    } else if (dtype == SPTRSV_F32) {
+        if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
+        st = plain_solve<float>(p, p->d.val_hi, p->d.diag_hi, b, x, nrhs, ld, o, s, c);
+    } else {
+        return fail(SPTRSV_ERR_ARG, "dtype must be SPTRSV_F64 or SPTRSV_F32");
+    }
+    if (st) return st;
+    if (report) {
+        Ctl ctl;
+        CUDA_TRY(cudaMemcpyAsync(&ctl, p->d.counters, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        std::memset(report, 0, sizeof(*report));
+        report->status = ctl.status;
+        report->sweeps = 1;
+        report->barriers = int64_t(ctl.barriers);
+        report->flag_waits = int64_t(ctl.flag_waits);
+        report->sync = c.sync;
+        report->lanes = c.lanes;
+        report->grid = c.grid;
+        report->threads = c.threads;
+        if (ctl.status) {
+            CUDA_TRY(cudaMemsetAsync(&reinterpret_cast<Ctl *>(p->d.counters)->status, 0, sizeof(int32_t), s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            return fail(ctl.status, "device reported " + std::string(sptrsv_status_string(ctl.status)));
+        }
+    }
+    return SPTRSV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sptrsv.h"
+
+namespace sptrsv {
+
+// Thread-local error message + status helper.
+int fail(int status, const std::string &msg);
+void clear_error();
+
+// Host-side result of the analysis (Sec. 2.2 DAG, Sec. 1 wavefronts, Sec. 3
+// schedule, Sec. 5 reordering) plus the execution structure the kernels walk.
+//
+// Execution structure: superstep s owns blocks [step_blk[s], step_blk[s+1]);
+// block b (one core's share of a superstep, Def. 2.1) owns phases
+// [blk_phase[b], blk_phase[b+1]); phase q owns device rows
+// [phase_row[q], phase_row[q+1]).  Rows of one phase are mutually
+// independent once every earlier phase of the block and every earlier
+// superstep is finished.  For the wavefront schedule every superstep is one
+// block with one phase.
+struct HostSchedule {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t nlevels = 0;
+    int32_t max_level_rows = 0;
+    int32_t mode = SPTRSV_SCHED_LEVELS;
+    int32_t k = 1;
+    int32_t S = 0;
+    std::vector<int32_t> level, sigma, pi;
+    std::vector<int32_t> perm;       // Sec. 5 order: position -> original row
+    std::vector<int32_t> dev_perm;   // device order: device row -> original row
+    std::vector<int32_t> step_blk, blk_phase, phase_row;
+    int32_t max_phase_rows = 0;
+    int32_t max_block_rows = 0;
+};
+
+struct DeviceBuffers {
+    // matrix in device-row order; column ids stay ORIGINAL row ids
+    int32_t *rp = nullptr;        // n + 1, off-diagonal entries only
+    int32_t *col = nullptr;       // nnz_off
+    double *val = nullptr;        // nnz_off (VALUES_F64)
+    double *diag = nullptr;       // n
+    float *val_hi = nullptr, *val_lo = nullptr;    // nnz_off (VALUES_F32)
+    float *diag_hi = nullptr, *diag_lo = nullptr;  // n
+    int32_t *perm = nullptr;      // n: device row -> original row
+    int32_t *step_blk = nullptr, *blk_phase = nullptr, *phase_row = nullptr;
+    // scratch
+    unsigned long long *counters = nullptr;  // [0] barrier, [1] barriers done, [2] flag waits,
+                                             // [3] work cursor, [4..] refinement norms
+    int32_t *status = nullptr;    // device status word (0 ok, else SPTRSV_ERR_*)
+    uint32_t *flags = nullptr;    // n ready flags holding the solve epoch
+    void *work = nullptr;         // refinement / internal vectors (grown on demand)
+    size_t work_bytes = 0;
+};
+
+}  // namespace sptrsv
+
+struct sptrsv_plan {
+    sptrsv::HostSchedule h;
+    int32_t values = 0;
+    int32_t device = -1;
+    int32_t num_sms = 0;
+    int64_t nnz_off = 0;
+    int64_t device_bytes = 0;
+    double analyze_ms = 0.0;
+    uint32_t epoch = 0;           // ready-flag epoch, bumped per flagged sweep
+    int32_t sticky_status = 0;    // device error seen by an asynchronous solve
+    sptrsv::DeviceBuffers d;
+    // autotuner memo: best (sync, lanes, threads, blocks_per_sm) per (dtype, precision, nrhs class)
+    int32_t tuned[4][2][4][4];
+    bool tuned_valid[4] = {false, false, false, false};
+};
+
+namespace sptrsv {
+// analyze.cpp
+int validate_csr(const sptrsv_csr *A);
+int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h);
+// growlocal.cpp
+int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
+                           double alpha0, double growth, double L, double accept,
+                           int32_t *sigma, int32_t *pi);
+// device.cu
+int upload_plan(sptrsv_plan *p, const sptrsv_csr *A);
+void free_device(sptrsv_plan *p);
+int device_sm_count(int device, int32_t *out);
+}  // namespace sptrsv

@@ -1,0 +1,151 @@
+"""Host-side analysis of the library against the oracle (CPU only, no GPU needed).
+
+The library is loaded through its C ABI and asked for a host-only plan
+(device = -1), so the schedules and permutations it exports can be compared
+bit for bit with the oracle's on any machine.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+sp = pytest.importorskip("paper_2503_05408_gb300")
+
+
+@pytest.fixture(scope="module")
+def L():
+    try:
+        return sp.lib()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+
+
+def test_library_exports_every_declared_symbol(L):
+    import re
+    import os
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "sptrsv.h")).read()
+    names = set(re.findall(r"\b(sptrsv_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    for name in sorted(names):
+        assert hasattr(L, name), f"{name} declared in include/sptrsv.h but not exported"
+
+
+def _host_plan(A, **kw):
+    return sp.Plan(A, device=-1, **kw)
+
+
+CASES = {
+    "fig1_1": lambda: W.from_pattern(6, [(1, 0), (2, 1), (3, 1), (4, 2), (5, 3)]),
+    "lap2d_64": lambda: W.laplace2d_lower(4096, 64),
+    "lap3d_20": lambda: W.laplace3d_lower(8000, 20),
+    "random_50k": lambda: W.random_window_lower(50_000, 6, 20000, 0),
+    "banded_30k": lambda: W.random_window_lower(30_000, 4, 64, 2),
+    "er_20k": lambda: W.erdos_renyi_lower(20_000, 2e-4, 1),
+    "nb_20k": lambda: W.narrow_band_lower(20_000, 0.05, 20, 1),
+    "diag_1000": lambda: W.from_pattern(1000, []),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_levels_and_level_schedule_bit_exact(L, name):
+    A = CASES[name]()
+    p = _host_plan(A, mode="levels")
+    ex = p.export()
+    lv, nlev = oracle.levels(A)
+    assert np.array_equal(ex.level, lv)
+    s, pi, S = oracle.level_schedule(A)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert np.array_equal(ex.perm, oracle.permutation(s, pi))
+    st = p.stats()
+    assert st["levels"] == nlev and st["supersteps"] == S and st["k"] == 1
+    assert st["avg_wavefront"] == pytest.approx(A.n / nlev)
+    assert oracle.check_schedule(A, ex.sigma, ex.pi, 1, strict=True) == []
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("k", [1, 2, 7, 22, 152])
+def test_growlocal_bit_exact(L, name, k):
+    A = CASES[name]()
+    p = _host_plan(A, mode="growlocal", k=k)
+    ex = p.export()
+    s, pi, S = oracle.growlocal(A, k)
+    assert np.array_equal(ex.sigma, s)
+    assert np.array_equal(ex.pi, pi)
+    assert np.array_equal(ex.perm, oracle.permutation(s, pi))
+    assert p.stats()["supersteps"] == S
+    assert oracle.check_schedule(A, ex.sigma, ex.pi, k) == []
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_growlocal_bit_exact_random_parameters(L, seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 3000))
+    kind = seed % 3
+    if kind == 0:
+        A = W.erdos_renyi_lower(n, float(rng.uniform(1e-4, 2e-2)), seed)
+    elif kind == 1:
+        A = W.narrow_band_lower(n, float(rng.uniform(0.02, 0.2)), float(rng.uniform(3, 40)), seed)
+    else:
+        A = W.random_window_lower(n, int(rng.integers(1, 8)), int(rng.integers(8, 2000)), seed)
+    k = int(rng.integers(1, 40))
+    kw = dict(alpha0=float(rng.choice([1.0, 2.0, 7.0, 20.0])), growth=float(rng.choice([1.2, 1.5, 2.0])),
+              L=float(rng.choice([0.0, 10.0, 500.0, 5000.0])), accept=float(rng.choice([0.9, 0.97, 1.0])))
+    p = _host_plan(A, mode="growlocal", k=k, **kw)
+    ex = p.export()
+    s, pi, S = oracle.growlocal(A, k, **kw)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert np.array_equal(ex.perm, oracle.permutation(s, pi))
+
+
+def test_growlocal_bit_exact_er_100k(L):
+    A = W.erdos_renyi_lower(100_000, 5e-4, 3)
+    p = _host_plan(A, mode="growlocal", k=22)
+    ex = p.export()
+    s, pi, S = oracle.growlocal(A, 22)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+
+
+@pytest.mark.parametrize("bad,code", [
+    ("zero_diag", sp.ERR_ZERO_DIAG), ("upper", sp.ERR_NOT_LOWER), ("unsorted", sp.ERR_UNSORTED_OR_DUP),
+    ("dup", sp.ERR_UNSORTED_OR_DUP), ("no_diag", sp.ERR_ZERO_DIAG), ("rowptr", sp.ERR_ARG),
+])
+def test_validation_errors(L, bad, code):
+    A = W.laplace2d_lower(64, 8)
+    rp, c, v = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    r = 20
+    lo, hi = rp[r], rp[r + 1]
+    if bad == "zero_diag":
+        v[hi - 1] = 0.0
+    elif bad == "upper":
+        c[hi - 1] = r + 1
+    elif bad == "unsorted":
+        c[lo], c[lo + 1] = c[lo + 1], c[lo]
+    elif bad == "dup":
+        c[lo + 1] = c[lo]
+    elif bad == "no_diag":
+        c[hi - 1] = r - 2
+        c[lo:hi - 1] = [r - 12, r - 5][: hi - 1 - lo]
+    elif bad == "rowptr":
+        rp[-1] += 1
+    B = W.CSR(A.n, rp, c, v)
+    with pytest.raises(sp.SptrsvError) as e:
+        _host_plan(B)
+    assert e.value.status == code
+
+
+def test_host_only_plan_refuses_to_solve(L):
+    A = W.laplace2d_lower(64, 8)
+    p = _host_plan(A)
+    o = sp.solve_opts()
+    rep = sp.Report()
+    st = L.sptrsv_solve(p.handle, 1, 1, 1, 64, sp.F64, None, 0, None)
+    assert st == sp.ERR_NO_DEVICE
+    assert b"host-only" in L.sptrsv_last_error()
+
+
+def test_stats_on_configs(L):
+    A = W.laplace3d_lower(160 ** 3, 160)
+    p = _host_plan(A)
+    st = p.stats()
+    assert st["levels"] == 478 and st["n"] == 4_096_000 and st["nnz"] == 16_307_200

@@ -1,0 +1,162 @@
+"""GPU parity of the superstep-scheduled solve against the CPU oracle.
+
+Every case compares the library's x (CUDA kernels through the C ABI) with the
+oracle's sequential FP64 forward substitution (Eq. 2.1) element by element:
+normwise relative error <= 1e-12 in FP64 (the summation order differs from
+the oracle's, so results are not bit-identical), and a bound derived from
+FP32 rounding for FP32 solves.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+sp = pytest.importorskip("paper_2503_05408_gb300")
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sp.lib()
+    torch.cuda.init()
+
+
+def to_dev(b, dtype=torch.float64, ld=None):
+    """Column-major device copy of a (n, nrhs) array, optional padded leading dimension."""
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    n, r = b.shape
+    ld = ld or n
+    buf = torch.zeros((r, ld), dtype=dtype, device="cuda")
+    buf[:, :n] = torch.from_numpy(np.ascontiguousarray(b.T)).to(dtype)
+    return buf.T[:n] if ld == n else buf.T[:n, :]
+
+
+def solve_gpu(plan, b_np, dtype=torch.float64, ld=None, **opts):
+    b = to_dev(b_np, dtype, ld)
+    x = to_dev(np.full(np.shape(b_np), np.nan).reshape(b.shape[0], -1), dtype, ld)
+    x = x.reshape(b.shape) if b.dim() == 1 else x
+    x, rep = plan.solve(b, x, **opts)
+    torch.cuda.synchronize()
+    return x.double().cpu().numpy(), rep
+
+
+SMALL = {
+    "lap2d_64x64": lambda: W.laplace2d_lower(4096, 64),
+    "lap3d_24": lambda: W.laplace3d_lower(24 ** 3, 24),
+    "random_60k": lambda: W.random_window_lower(60_000, 6, 20000, 0),
+    "banded_20k": lambda: W.random_window_lower(20_000, 4, 64, 1),
+    "er_30k": lambda: W.make_dominant(W.erdos_renyi_lower(30_000, 3e-4, 2)),
+    "nb_20k": lambda: W.make_dominant(W.narrow_band_lower(20_000, 0.05, 20, 3)),
+    "dense_rows": lambda: W.random_window_lower(5_000, 40, 200, 4),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_f64_levels_parity(name, sync, lanes):
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=11)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A, mode="levels")
+    x, rep = solve_gpu(plan, b, sync=sync, lanes=lanes)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+    if sync == "grid":
+        assert rep["barriers"] == plan.stats()["supersteps"] - 1
+
+
+@pytest.mark.parametrize("name", ["lap2d_64x64", "er_30k", "nb_20k", "banded_20k"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("k", [1, 8, 152])
+def test_f64_growlocal_parity(name, sync, k):
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=12)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A, mode="growlocal", k=k)
+    ex = plan.export()
+    s, pi, S = oracle.growlocal(A, k)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    x, rep = solve_gpu(plan, b, sync=sync)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0)])
+def test_multi_rhs(sync, nrhs, ld_pad):
+    A = W.laplace3d_lower(20 ** 3, 20)
+    xs, b = W.manufactured_rhs(A, nrhs, seed=13)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    x, rep = solve_gpu(plan, b, ld=A.n + ld_pad, sync=sync, lanes=1)
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+def test_f32_solve():
+    # FP32 values and arithmetic: the error is bounded by ~n_levels * eps32 * growth;
+    # these diagonally dominant factors stay far below 1e-4.
+    for A in (W.laplace2d_lower(4096, 64), W.random_window_lower(40_000, 6, 20000, 5)):
+        xs, b = W.manufactured_rhs(A, 1, seed=14)
+        xo = oracle.solve(A, b)
+        plan = sp.Plan(A)
+        for sync in ("grid", "flags", "cta"):
+            x, rep = solve_gpu(plan, b, dtype=torch.float32, sync=sync)
+            assert oracle.rel_error(x, xo) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1000])
+def test_edge_sizes(n):
+    A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
+    b = np.ones((n, 1))
+    plan = sp.Plan(A)
+    for sync in ("grid", "flags", "cta"):
+        x, rep = solve_gpu(plan, b, sync=sync)
+        assert np.allclose(x[:, 0], 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)
+
+
+def test_diagonal_only_is_one_superstep():
+    A = W.from_pattern(100_000, [])
+    A.val[:] = np.linspace(0.5, 2.0, A.n)
+    b = np.random.default_rng(0).standard_normal((A.n, 1))
+    plan = sp.Plan(A)
+    for sync in ("grid", "flags", "cta"):
+        x, rep = solve_gpu(plan, b, sync=sync)
+        assert np.array_equal(x[:, 0], b[:, 0] / A.val)      # one IEEE division per row
+    assert rep["barriers"] == 0
+
+
+def test_timeout_is_reported_and_context_survives():
+    # A 1 ns wait limit makes every grid barrier give up: the kernel records
+    # SPTRSV_ERR_TIMEOUT and returns (no trap); the next solve works normally.
+    A = W.laplace2d_lower(4096 * 4, 128)
+    xs, b = W.manufactured_rhs(A, 1, seed=15)
+    plan = sp.Plan(A)
+    with pytest.raises(sp.SptrsvError) as e:
+        solve_gpu(plan, b, sync="grid", timeout_s=1e-9)
+    assert e.value.status == sp.ERR_TIMEOUT
+    x, rep = solve_gpu(plan, b, sync="grid")
+    assert oracle.rel_error(x, oracle.solve(A, b)) <= F64_TOL
+
+
+@pytest.mark.parametrize("cfg", ["small_2d", "random_1m", "lap3d_160"])
+def test_full_size_configs_f64(cfg):
+    if cfg == "small_2d":
+        A, xs, b = W.config_small_2d()
+    elif cfg == "random_1m":
+        A, xs, b = W.config_random_1m()
+    else:
+        A, xs, b = W.config_3d_160()
+    xo = oracle.solve(A, b)
+    assert oracle.rel_error(xo, xs) < 1e-13
+    plan = sp.Plan(A)
+    for sync in ("grid", "flags"):
+        x, rep = solve_gpu(plan, b, sync=sync)
+        assert oracle.rel_error(x, xo) <= F64_TOL

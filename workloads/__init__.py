@@ -36,7 +36,7 @@ import numpy as np
 
 __all__ = [
     "CSR", "laplace2d_lower", "laplace3d_lower", "random_window_lower",
-    "erdos_renyi_lower", "narrow_band_lower", "from_pattern", "manufactured_rhs",
+    "erdos_renyi_lower", "narrow_band_lower", "make_dominant", "from_pattern", "manufactured_rhs",
     "config_small_2d", "config_random_1m", "config_3d_160", "batch_factor",
     "serve_factor", "batch_sizes", "serve_sizes", "serve_requests",
 ]
@@ -114,10 +114,17 @@ def laplace3d_lower(n: int, width: int | None = None, diag: float = 6.0, off: fl
 
 
 def _distinct_sorted_draws(rng, lo, width, per_row):
-    """Per row: ``per_row`` distinct sorted integers in [lo, lo + width) by rejection."""
+    """Per row: ``per_row`` distinct sorted integers in [lo, lo + width).
+
+    Narrow windows (where a batch of independent draws would rarely be distinct)
+    draw without replacement row by row; the rest use vectorised rejection.
+    """
     m = lo.size
     out = np.empty((m, per_row), dtype=np.int64)
-    pending = np.arange(m)
+    narrow = np.nonzero(width < per_row * per_row)[0]
+    for r in narrow:
+        out[r] = np.sort(rng.choice(int(width[r]), size=per_row, replace=False))
+    pending = np.nonzero(width >= per_row * per_row)[0]
     while pending.size:
         d = rng.integers(0, width[pending, None], size=(pending.size, per_row))
         d.sort(axis=1)
@@ -199,6 +206,19 @@ def narrow_band_lower(n: int, p: float, B: float, seed: int) -> CSR:
     offvals, diag = _er_values(rng, offcols.size, n)
     return _assemble(n, counts, offcols, offvals, diag, f"nb_n{n}_p{p}_B{B}_s{seed}",
                      {"kind": "narrow_band", "p": p, "B": B, "seed": seed})
+
+
+def make_dominant(A: CSR) -> CSR:
+    """Same pattern and off-diagonal values, diagonal replaced by 1 + sum |off-diagonal|
+    (strictly diagonally dominant, so FP64 solves stay at rounding-level error)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag_pos = A.rowptr[1:] - 1
+    off = np.ones(A.val.size, dtype=bool)
+    off[diag_pos] = False
+    absum = np.bincount(rows[off], weights=np.abs(A.val[off]), minlength=A.n)
+    val = A.val.copy()
+    val[diag_pos] = 1.0 + absum
+    return CSR(A.n, A.rowptr, A.col, val, A.name + "_dom", dict(A.meta))
 
 
 def from_pattern(n: int, entries, diag: float = 1.0, off: float = -1.0) -> CSR:
