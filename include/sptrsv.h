@@ -193,6 +193,17 @@ int sptrsv_solve(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_
                  int32_t dtype, const sptrsv_solve_opts *opts, sptrsv_stream stream,
                  sptrsv_report *report);
 
+/* Autotuner: time every candidate launch shape (sync mode x lanes per row x threads x
+ * blocks per SM) of sptrsv_solve on the caller's b/x with CUDA events (x is overwritten),
+ * remember the fastest in the plan for this (dtype, precision, nrhs class), and return it.
+ * Later sptrsv_solve calls with opts->sync == SPTRSV_SYNC_AUTO use the remembered shape.
+ *   base    : fixed fields (precision, tolerances, timeout); may be NULL.
+ *   best    : receives the winning options (may be NULL); best_ms its time (may be NULL).
+ * Synchronises `stream`.  Errors as sptrsv_solve; LAUNCH if no candidate could run. */
+int sptrsv_autotune(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_t ld,
+                    int32_t dtype, const sptrsv_solve_opts *base, sptrsv_stream stream,
+                    sptrsv_solve_opts *best, double *best_ms);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

@@ -102,6 +102,8 @@ def lib():
             "sptrsv_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
             "sptrsv_solve": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
                                             ctypes.POINTER(Report)]),
+            "sptrsv_autotune": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
+                                               ctypes.POINTER(SolveOpts), ctypes.POINTER(dbl)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -206,9 +208,21 @@ class Plan:
         _check(lib().sptrsv_plan_export(self.handle, *[_ptr(a) for a in arrs]))
         return ScheduleExport(*arrs)
 
-    def solve(self, b, x=None, *, stream=None, report=True, **opts):
-        """Solve L x = b for a CUDA tensor ``b`` of shape (n,) or (n, nrhs) column-major
-        (stride (1, ld)); ``x`` is allocated like ``b`` if not given.  Returns (x, report)."""
+    def autotune(self, b, x, *, stream=None, **base):
+        """Time the candidate launch shapes on (b, x) and remember the fastest in the plan;
+        returns the winning options as a dict (usable as ``solve(**opts)``)."""
+        nrhs, ld, dtype = self._shape(b, x)
+        best = SolveOpts()
+        ms = ctypes.c_double()
+        _check(lib().sptrsv_autotune(self.handle, _ptr(b), _ptr(x), nrhs, ld, dtype,
+                                     ctypes.byref(solve_opts(**base)), _stream_handle(stream),
+                                     ctypes.byref(best), ctypes.byref(ms)))
+        out = {"sync": best.sync, "lanes": best.lanes, "threads": best.threads,
+               "blocks_per_sm": best.blocks_per_sm}
+        self.tuned_ms = ms.value
+        return out
+
+    def _shape(self, b, x):
         import torch
         if not (isinstance(b, torch.Tensor) and b.is_cuda):
             raise TypeError("b must be a CUDA tensor")
@@ -231,10 +245,17 @@ class Plan:
             raise ValueError("b must be 1-D or 2-D")
         if b.shape[0] != self.n:
             raise ValueError("b has the wrong number of rows")
+        if x is not None and (x.dtype != b.dtype or x.shape != b.shape or x.stride() != b.stride()):
+            raise ValueError("x must match b in dtype, shape and strides")
+        return nrhs, ld, dtype
+
+    def solve(self, b, x=None, *, stream=None, report=True, **opts):
+        """Solve L x = b for a CUDA tensor ``b`` of shape (n,) or (n, nrhs) column-major
+        (stride (1, ld)); ``x`` is allocated like ``b`` if not given.  Returns (x, report)."""
+        import torch
+        nrhs, ld, dtype = self._shape(b, x)
         if x is None:
             x = torch.empty_strided(b.shape, b.stride(), dtype=b.dtype, device=b.device)
-        if x.dtype != b.dtype or x.shape != b.shape or x.stride() != b.stride():
-            raise ValueError("x must match b in dtype, shape and strides")
         rep = Report()
         o = solve_opts(**opts)
         st = lib().sptrsv_solve(self.handle, _ptr(b), _ptr(x), int(nrhs), int(ld), dtype,

@@ -167,8 +167,23 @@ int auto_lanes(const sptrsv_plan *p) {
     return 32;
 }
 
+int tune_slot(int32_t dtype, int32_t precision, int32_t nrhs) {
+    const int r = nrhs <= 1 ? 0 : nrhs <= 4 ? 1 : nrhs <= 16 ? 2 : 3;
+    return (dtype == SPTRSV_F32 ? 1 : 0) * 8 + (precision ? 4 : 0) + r;
+}
+
 template <typename T>
-int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o, LaunchCfg &c) {
+int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, LaunchCfg &c) {
+    sptrsv_solve_opts o = o_in;
+    if (o.sync == SPTRSV_SYNC_AUTO && p->tuned_slot >= 0) {
+        const TunedCfg &t = p->tuned[p->tuned_slot];
+        if (t.valid) {
+            o.sync = t.sync;
+            if (!o.lanes) o.lanes = t.lanes;
+            if (!o.threads) o.threads = t.threads;
+            if (!o.blocks_per_sm) o.blocks_per_sm = t.blocks_per_sm;
+        }
+    }
     c.sync = o.sync;
     if (c.sync == SPTRSV_SYNC_AUTO) {
         if (p->h.n <= 8192) c.sync = SPTRSV_SYNC_CTA;
@@ -243,6 +258,19 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *diag) {
     return a;
 }
 
+int check_solve_args(const sptrsv_plan *p, const void *b, const void *x, int32_t nrhs, int64_t ld,
+                     int32_t dtype, const sptrsv_solve_opts &o) {
+    if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SPTRSV_ERR_NO_DEVICE, "plan was analysed host-only");
+    if (nrhs < 0 || (p->h.n > 0 && nrhs > 0 && (!b || !x)) || ld < std::max<int64_t>(p->h.n, 1))
+        return fail(SPTRSV_ERR_ARG, "bad b/x/nrhs/ld");
+    if (dtype != SPTRSV_F64 && dtype != SPTRSV_F32) return fail(SPTRSV_ERR_ARG, "dtype must be SPTRSV_F64 or SPTRSV_F32");
+    if (!(o.timeout_s > 0.0)) return fail(SPTRSV_ERR_ARG, "timeout_s must be positive");
+    if (o.precision != SPTRSV_PREC_F64 && o.precision != SPTRSV_PREC_F32_REFINE)
+        return fail(SPTRSV_ERR_ARG, "unknown precision mode");
+    return SPTRSV_OK;
+}
+
 uint32_t next_epoch(sptrsv_plan *p, cudaStream_t s) {
     if (++p->epoch == 0) {                      // wrapped: clear the flags once
         cudaMemsetAsync(p->d.flags, 0, std::max<size_t>(size_t(p->h.n), 1) * sizeof(uint32_t), s);
@@ -269,6 +297,41 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *diag, const void *b, void
     return launch<T>(p, c, a, s);
 }
 
+
+int solve_impl(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
+               const sptrsv_solve_opts &o, cudaStream_t s, LaunchCfg &c) {
+    p->tuned_slot = tune_slot(dtype, o.precision, nrhs);
+    if (dtype == SPTRSV_F64) {
+        if (o.precision == SPTRSV_PREC_F64) {
+            if (!(p->values & SPTRSV_VALUES_F64)) return fail(SPTRSV_ERR_ARG, "plan has no FP64 values");
+            return plain_solve<double>(p, p->d.val, p->d.diag, b, x, nrhs, ld, o, s, c);
+        }
+        return fail(SPTRSV_ERR_ARG, "precision mode not available yet");
+    }
+    if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
+    return plain_solve<float>(p, p->d.val_hi, p->d.diag_hi, b, x, nrhs, ld, o, s, c);
+}
+
+int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_report *report) {
+    Ctl ctl;
+    CUDA_TRY(cudaMemcpyAsync(&ctl, p->d.counters, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::memset(report, 0, sizeof(*report));
+    report->status = ctl.status;
+    report->sweeps = 1;
+    report->barriers = int64_t(ctl.barriers);
+    report->flag_waits = int64_t(ctl.flag_waits);
+    report->sync = c.sync;
+    report->lanes = c.lanes;
+    report->grid = c.grid;
+    report->threads = c.threads;
+    if (ctl.status) {
+        CUDA_TRY(cudaMemsetAsync(&reinterpret_cast<Ctl *>(p->d.counters)->status, 0, sizeof(int32_t), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return fail(ctl.status, "device reported " + std::string(sptrsv_status_string(ctl.status)));
+    }
+    return SPTRSV_OK;
+}
 }  // namespace
 }  // namespace sptrsv
 
@@ -291,57 +354,97 @@ void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
 int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
                  const sptrsv_solve_opts *opts, sptrsv_stream stream, sptrsv_report *report) {
     clear_error();
-    if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
-    if (p->device < 0) return fail(SPTRSV_ERR_NO_DEVICE, "plan was analysed host-only");
     sptrsv_solve_opts o;
     sptrsv_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (nrhs < 0 || (p->h.n > 0 && nrhs > 0 && (!b || !x)) || ld < std::max<int64_t>(p->h.n, 1))
-        return fail(SPTRSV_ERR_ARG, "bad b/x/nrhs/ld");
-    if (!(o.timeout_s > 0.0)) return fail(SPTRSV_ERR_ARG, "timeout_s must be positive");
+    int st = check_solve_args(p, b, x, nrhs, ld, dtype, o);
+    if (st) return st;
     DeviceGuard g(p->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    LaunchCfg c{};
-    int st = SPTRSV_OK;
     if (p->h.n == 0 || nrhs == 0) {
-        if (report) {
-            std::memset(report, 0, sizeof(*report));
-        }
+        if (report) std::memset(report, 0, sizeof(*report));
         return SPTRSV_OK;
     }
-    if (dtype == SPTRSV_F64) {
-        if (o.precision == SPTRSV_PREC_F64) {
-            if (!(p->values & SPTRSV_VALUES_F64)) return fail(SPTRSV_ERR_ARG, "plan has no FP64 values");
-            st = plain_solve<double>(p, p->d.val, p->d.diag, b, x, nrhs, ld, o, s, c);
-        } else {
-            return fail(SPTRSV_ERR_ARG, "precision mode not available yet");
-        }
-    } else if (dtype == SPTRSV_F32) {
-        if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
-        st = plain_solve<float>(p, p->d.val_hi, p->d.diag_hi, b, x, nrhs, ld, o, s, c);
-    } else {
-        return fail(SPTRSV_ERR_ARG, "dtype must be SPTRSV_F64 or SPTRSV_F32");
-    }
+    LaunchCfg c{};
+    st = solve_impl(p, b, x, nrhs, ld, dtype, o, s, c);
     if (st) return st;
-    if (report) {
-        Ctl ctl;
-        CUDA_TRY(cudaMemcpyAsync(&ctl, p->d.counters, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        std::memset(report, 0, sizeof(*report));
-        report->status = ctl.status;
-        report->sweeps = 1;
-        report->barriers = int64_t(ctl.barriers);
-        report->flag_waits = int64_t(ctl.flag_waits);
-        report->sync = c.sync;
-        report->lanes = c.lanes;
-        report->grid = c.grid;
-        report->threads = c.threads;
-        if (ctl.status) {
-            CUDA_TRY(cudaMemsetAsync(&reinterpret_cast<Ctl *>(p->d.counters)->status, 0, sizeof(int32_t), s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            return fail(ctl.status, "device reported " + std::string(sptrsv_status_string(ctl.status)));
+    if (report) return read_report(p, c, s, report);
+    return SPTRSV_OK;
+}
+
+int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
+                    const sptrsv_solve_opts *base, sptrsv_stream stream, sptrsv_solve_opts *best,
+                    double *best_ms) {
+    clear_error();
+    sptrsv_solve_opts o;
+    sptrsv_solve_opts_default(&o);
+    if (base) o = *base;
+    int st = check_solve_args(p, b, x, nrhs, ld, dtype, o);
+    if (st) return st;
+    if (p->h.n == 0 || nrhs == 0) return fail(SPTRSV_ERR_ARG, "nothing to tune");
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<sptrsv_solve_opts> cands;
+    const bool small = int64_t(p->h.n) * nrhs <= 400000;
+    const int lane_set[] = {1, 4, 8, 32};
+    for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
+        if (sync == SPTRSV_SYNC_CTA && !small) continue;
+        for (int lanes : lane_set) {
+            if (sync == SPTRSV_SYNC_CTA) {
+                for (int t : {256, 512, 1024}) {
+                    sptrsv_solve_opts c = o;
+                    c.sync = sync; c.lanes = lanes; c.threads = t; c.blocks_per_sm = 0;
+                    cands.push_back(c);
+                }
+            } else {
+                for (int t : {128, 256, 512})
+                    for (int bps : {1, 2}) {
+                        sptrsv_solve_opts c = o;
+                        c.sync = sync; c.lanes = lanes; c.threads = t; c.blocks_per_sm = bps;
+                        cands.push_back(c);
+                    }
+            }
         }
     }
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best_t = 1e30;
+    sptrsv_solve_opts best_o = o;
+    for (const sptrsv_solve_opts &c : cands) {
+        LaunchCfg lc{};
+        if (solve_impl(p, b, x, nrhs, ld, dtype, c, s, lc)) continue;     // e.g. not co-resident
+        sptrsv_report rep;
+        if (read_report(p, lc, s, &rep)) continue;
+        double t = 1e30;
+        for (int rep_i = 0; rep_i < 3; ++rep_i) {
+            cudaEventRecord(e0, s);
+            if (solve_impl(p, b, x, nrhs, ld, dtype, c, s, lc)) break;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t = std::min(t, double(ms));
+            if (t > 4.0 * best_t) break;
+        }
+        if (t < best_t) {
+            best_t = t;
+            best_o = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    clear_error();
+    if (best_t >= 1e30) return fail(SPTRSV_ERR_LAUNCH, "no candidate configuration ran");
+    TunedCfg &m = p->tuned[tune_slot(dtype, o.precision, nrhs)];
+    m.valid = true;
+    m.sync = best_o.sync;
+    m.lanes = best_o.lanes;
+    m.threads = best_o.threads;
+    m.blocks_per_sm = best_o.blocks_per_sm;
+    m.ms = best_t;
+    if (best) *best = best_o;
+    if (best_ms) *best_ms = best_t;
     return SPTRSV_OK;
 }
 

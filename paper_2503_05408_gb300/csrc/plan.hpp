@@ -71,10 +71,17 @@ struct sptrsv_plan {
     uint32_t epoch = 0;           // ready-flag epoch, bumped per flagged sweep
     int32_t sticky_status = 0;    // device error seen by an asynchronous solve
     sptrsv::DeviceBuffers d;
-    // autotuner memo: best (sync, lanes, threads, blocks_per_sm) per (dtype, precision, nrhs class)
-    int32_t tuned[4][2][4][4];
-    bool tuned_valid[4] = {false, false, false, false};
+    // autotuner memo: best launch shape per (dtype, precision, nrhs class); the slot of the
+    // call being served is selected by sptrsv_solve before it picks a configuration
+    struct TunedCfg {
+        bool valid = false;
+        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0;
+        double ms = 0.0;
+    };
+    TunedCfg tuned[16];
+    int32_t tuned_slot = -1;
 };
+using TunedCfg = sptrsv_plan::TunedCfg;
 
 namespace sptrsv {
 // analyze.cpp
