@@ -204,6 +204,35 @@ int sptrsv_autotune(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int
                     int32_t dtype, const sptrsv_solve_opts *base, sptrsv_stream stream,
                     sptrsv_solve_opts *best, double *best_ms);
 
+/* --------------------------------------------------------- no allocation */
+/* Largest factor sptrsv_solve_csr_noalloc accepts (rows). */
+#define SPTRSV_NOALLOC_MAX_ROWS (1 << 20)
+
+/* Allocation-free solve for callers that cannot let a library call cudaMalloc
+ * (device memory drawn only from the caller's own pool or budget, or a
+ * latency-critical loop where an allocation may synchronise the device).  The
+ * paper has no counterpart: this is a deployment convenience.
+ *
+ * Solves L x = b for one right-hand side directly on a caller-owned DEVICE CSR
+ * factor (0-based, int32, columns strictly increasing, diagonal last and
+ * non-zero), rows taken in natural order with per-row ready flags - no
+ * analysis, no plan.  b and x are device vectors of n doubles; x must not
+ * overlap b or the factor.  Allocates nothing: its scratch (one ready flag per
+ * row plus 256 bytes of control words, 4 MiB + 256 B in all) is a fixed array
+ * that every GPU loading this library holds until the process exits.
+ *   - n > SPTRSV_NOALLOC_MAX_ROWS is rejected with SPTRSV_ERR_ARG.
+ *   - The first call on a device (with that device current) resolves the
+ *     array's device address once; make that first call before any stream
+ *     capture on the device.
+ *   - Every call shares the array; the flags keep the last call's epoch and
+ *     the control words are cleared at the start of each call.  Calls that
+ *     overlap on the GPU (e.g. on two streams) race: serialise them.
+ *   - The call synchronises `stream`.  Malformed factors are detected on the
+ *     device where they would break memory safety (SPTRSV_ERR_ARG,
+ *     SPTRSV_ERR_NOT_LOWER); waits are bounded (SPTRSV_ERR_TIMEOUT). */
+int sptrsv_solve_csr_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                             const double *val, const double *b, double *x, sptrsv_stream stream);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif
