@@ -113,6 +113,8 @@ typedef struct {
     double avg_wavefront;    /* n / levels (Sec. 6.2)                                      */
     int64_t device_bytes;    /* bytes resident on the device for this plan                 */
     double analyze_ms;       /* host wall time of sptrsv_analyze                           */
+    int32_t phases;          /* dependency-free row groups walked by the executors          */
+    int32_t ring_rows;       /* shared-memory x ring proven safe for one-block walks (0: none) */
 } sptrsv_stats;
 
 /* Analyse a factor (Sec. 2.2 DAG, Sec. 1 wavefronts, Sec. 3 schedule, Sec. 5
@@ -158,8 +160,9 @@ typedef struct {
     int32_t sync;        /* SPTRSV_SYNC_*                                                    */
     int32_t lanes;       /* lanes per row: 0 = auto, or 1, 2, 4, 8, 16, 32                   */
     int32_t precision;   /* SPTRSV_PREC_* for dtype F64 (dtype F32 always solves in FP32)    */
-    int32_t max_iters;   /* refinement: maximum correction sweeps after the first (6)        */
-    double refine_tol;   /* refinement stops when ||d||inf <= refine_tol * ||x||inf (1e-14)   */
+    int32_t max_iters;   /* refinement: maximum correction sweeps after the first (6, <= 14) */
+    double refine_tol;   /* refinement stops when ||d||inf <= refine_tol * ||x||inf or when the
+                            FP64 backward error of the iterate is <= refine_tol (1e-13)       */
     int32_t blocks_per_sm; /* persistent grid size per SM; 0 = auto                          */
     int32_t threads;     /* threads per block; 0 = auto                                      */
     double timeout_s;    /* limit of every bounded device wait, seconds (default 2.0)         */
@@ -177,6 +180,8 @@ typedef struct {
     int32_t lanes;         /* lanes per row actually used                                     */
     int32_t grid;          /* thread blocks launched                                          */
     int32_t threads;       /* threads per block                                               */
+    double berr;           /* refinement: last normwise backward error max|r| /
+                              (||L||inf max|x| + max|b|) computed in FP64 (0 for a plain solve) */
 } sptrsv_report;
 
 /* Solve L X = B for nrhs right-hand sides (Eq. 2.1 in the plan's schedule).

@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("supersteps", ctypes.c_int32), ("k", ctypes.c_int32), ("max_level_rows", ctypes.c_int32),
                 ("avg_wavefront", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("analyze_ms", ctypes.c_double)]
+                ("analyze_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("ring_rows", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -69,7 +69,8 @@ class SolveOpts(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("barriers", ctypes.c_int64),
                 ("flag_waits", ctypes.c_int64), ("dnorm", ctypes.c_double), ("sync", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("berr", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -3,6 +3,7 @@
 // reordering and the execution structure the device kernels walk.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -82,6 +83,40 @@ void stable_bucket(std::vector<int32_t> &ids, const std::vector<int32_t> &key, i
     std::vector<int32_t> out(ids.size());
     for (int32_t v : ids) out[start[key[v]]++] = v;
     ids.swap(out);
+}
+
+// Shared-memory ring for the single-block walker: x[v] lives in slot
+// v mod W from the phase that writes it until the last phase that reads it
+// (its last child).  W is safe iff no two rows sharing a slot are live in the
+// same phase; rows are visited in phase order, so comparing each row with the
+// previous occupant of its slot suffices.
+int32_t ring_window(const sptrsv_csr *A, const HostSchedule &h) {
+    const int32_t n = h.n;
+    if (n == 0) return 0;
+    std::vector<int32_t> phase_of(n), last_use(n);
+    const int32_t nph = int32_t(h.phase_row.size()) - 1;
+    for (int32_t q = 0; q < nph; ++q)
+        for (int32_t r = h.phase_row[q]; r < h.phase_row[q + 1]; ++r) phase_of[h.dev_perm[r]] = q;
+    for (int32_t v = 0; v < n; ++v) last_use[v] = phase_of[v];
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t q = A->rowptr[v]; q < A->rowptr[v + 1] - 1; ++q) {
+            const int32_t c = A->col[q];
+            last_use[c] = std::max(last_use[c], phase_of[v]);
+        }
+    constexpr int32_t kMaxRingRows = 1 << 15;
+    std::vector<int32_t> slot_last(kMaxRingRows);
+    for (int32_t W = 32; W <= kMaxRingRows; W <<= 1) {
+        std::fill(slot_last.begin(), slot_last.begin() + W, -1);
+        bool ok = true;
+        for (int32_t r = 0; r < n && ok; ++r) {
+            const int32_t v = h.dev_perm[r];
+            int32_t &prev = slot_last[v & (W - 1)];
+            if (prev >= phase_of[v]) ok = false;
+            prev = last_use[v];
+        }
+        if (ok) return W;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -175,6 +210,7 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
     }
     if (int32_t(h.step_blk.size()) - 1 != h.S)
         return fail(SPTRSV_ERR_ARG, "internal: superstep count mismatch");
+    h.ring_rows = n <= (1 << 20) ? ring_window(A, h) : 0;
     return SPTRSV_OK;
 }
 
@@ -257,6 +293,11 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     }
     p->values = o.values;
     p->device = o.device;
+    for (int32_t i = 0; i < csr->n; ++i) {
+        double rs = 0.0;
+        for (int32_t q = csr->rowptr[i]; q < csr->rowptr[i + 1]; ++q) rs += std::abs(csr->val[q]);
+        p->lnorm = std::max(p->lnorm, rs);
+    }
     p->num_sms = sms;
     p->nnz_off = csr->nnz - csr->n;
     if (o.device >= 0) {
@@ -283,6 +324,8 @@ int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
     out->avg_wavefront = p->h.nlevels ? double(p->h.n) / p->h.nlevels : 0.0;
     out->device_bytes = p->device_bytes;
     out->analyze_ms = p->analyze_ms;
+    out->phases = int32_t(p->h.phase_row.size()) - 1;
+    out->ring_rows = p->h.ring_rows;
     return SPTRSV_OK;
 }
 

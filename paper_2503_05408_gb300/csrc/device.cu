@@ -135,37 +135,69 @@ namespace {
 
 template <typename T>
 using Kern = void (*)(SolveArgs<T>);
+template <typename T>
+using WalkKern = void (*)(SolveArgs<T>, int, int);
+
+// Register tile per lane for each supported lanes-per-row value.
+constexpr int tile_for(int lanes) { return lanes == 1 ? 8 : lanes == 2 ? 4 : lanes == 4 ? 2 : 1; }
+
+bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 32; }
 
 template <typename T>
-Kern<T> pick_kernel(int sync, int lanes) {
-#define SPTRSV_LANES_CASE(L)                                          \
-    case L:                                                           \
-        return sync == SPTRSV_SYNC_GRID    ? k_grid<T, L>             \
-               : sync == SPTRSV_SYNC_FLAGS ? k_flags<T, L>            \
-                                           : k_cta<T, L>;
+Kern<T> flags_kernel(int lanes) {
     switch (lanes) {
-        SPTRSV_LANES_CASE(1)
-        SPTRSV_LANES_CASE(2)
-        SPTRSV_LANES_CASE(4)
-        SPTRSV_LANES_CASE(8)
-        SPTRSV_LANES_CASE(16)
-        SPTRSV_LANES_CASE(32)
+        case 1: return k_flags<T, 1, tile_for(1)>;
+        case 2: return k_flags<T, 2, tile_for(2)>;
+        case 4: return k_flags<T, 4, tile_for(4)>;
+        case 8: return k_flags<T, 8, tile_for(8)>;
+        case 32: return k_flags<T, 32, tile_for(32)>;
         default: return nullptr;
     }
-#undef SPTRSV_LANES_CASE
+}
+template <typename T>
+Kern<T> blocks_kernel(int lanes) {
+    switch (lanes) {
+        case 1: return k_blocks<T, 1>;
+        case 2: return k_blocks<T, 2>;
+        case 4: return k_blocks<T, 4>;
+        case 8: return k_blocks<T, 8>;
+        case 32: return k_blocks<T, 32>;
+        default: return nullptr;
+    }
+}
+template <typename T, bool GRID, bool RING>
+WalkKern<T> walk_kernel(int lanes) {
+    switch (lanes) {
+        case 1: return k_walk<T, 1, tile_for(1), GRID, RING>;
+        case 2: return k_walk<T, 2, tile_for(2), GRID, RING>;
+        case 4: return k_walk<T, 4, tile_for(4), GRID, RING>;
+        case 8: return k_walk<T, 8, tile_for(8), GRID, RING>;
+        case 32: return k_walk<T, 32, tile_for(32), GRID, RING>;
+        default: return nullptr;
+    }
 }
 
 struct LaunchCfg {
     int sync, lanes, threads, grid;
+    int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA)
+    int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
+    size_t smem;
 };
 
 int auto_lanes(const sptrsv_plan *p) {
     const double per_row = p->h.n ? double(p->nnz_off) / p->h.n : 0.0;
     if (per_row <= 4.0) return 1;
-    if (per_row <= 12.0) return 4;
-    if (per_row <= 32.0) return 8;
+    if (per_row <= 8.0) return 2;
+    if (per_row <= 16.0) return 8;
     return 32;
 }
+
+bool wide_phases(const sptrsv_plan *p) {
+    // every superstep is one block with one phase (the wavefront schedule)
+    return int32_t(p->h.phase_row.size()) - 1 == p->h.S;
+}
+
+constexpr size_t kRingBytesMax = 200 * 1024;
 
 int tune_slot(int32_t dtype, int32_t precision, int32_t nrhs) {
     const int r = nrhs <= 1 ? 0 : nrhs <= 4 ? 1 : nrhs <= 16 ? 2 : 3;
@@ -173,7 +205,19 @@ int tune_slot(int32_t dtype, int32_t precision, int32_t nrhs) {
 }
 
 template <typename T>
-int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, LaunchCfg &c) {
+const void *kernel_ptr(const LaunchCfg &c) {
+    switch (c.kind) {
+        case 0: return reinterpret_cast<const void *>(flags_kernel<T>(c.lanes));
+        case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false>(c.lanes));
+        case 2: return reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
+        default:
+            return c.win ? reinterpret_cast<const void *>(walk_kernel<T, false, true>(c.lanes))
+                         : reinterpret_cast<const void *>(walk_kernel<T, false, false>(c.lanes));
+    }
+}
+
+template <typename T>
+int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, LaunchCfg &c) {
     sptrsv_solve_opts o = o_in;
     if (o.sync == SPTRSV_SYNC_AUTO && p->tuned_slot >= 0) {
         const TunedCfg &t = p->tuned[p->tuned_slot];
@@ -187,24 +231,41 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, LaunchCfg &c) {
     c.sync = o.sync;
     if (c.sync == SPTRSV_SYNC_AUTO) {
         if (p->h.n <= 8192) c.sync = SPTRSV_SYNC_CTA;
-        else if (p->h.mode == SPTRSV_SCHED_LEVELS) c.sync = SPTRSV_SYNC_FLAGS;
-        else c.sync = SPTRSV_SYNC_GRID;
+        else c.sync = SPTRSV_SYNC_FLAGS;
     }
     c.lanes = o.lanes ? o.lanes : auto_lanes(p);
-    if (!pick_kernel<T>(c.sync, c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8, 16 or 32");
-    c.threads = o.threads ? o.threads : (c.sync == SPTRSV_SYNC_CTA ? 1024 : 256);
-    if (c.threads < 32 || c.threads > 1024 || c.threads % 32)
-        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
-    if (c.sync == SPTRSV_SYNC_CTA) {
+    if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
+    c.threads = o.threads ? o.threads : 256;
+    if (c.threads < 32 || c.threads > 512 || c.threads % 32)
+        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
+    c.win = 0;
+    c.smem = 0;
+    if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
+    else if (c.sync == SPTRSV_SYNC_GRID) c.kind = wide_phases(p) ? 1 : 2;
+    else if (c.sync == SPTRSV_SYNC_CTA) {
+        c.kind = 3;
+        const int w = p->h.ring_rows;
+        if (w > 0 && size_t(w) * size_t(nrhs) * sizeof(T) <= kRingBytesMax) {
+            c.win = w;
+            c.smem = size_t(w) * size_t(nrhs) * sizeof(T);
+        }
+    } else {
+        return fail(SPTRSV_ERR_ARG, "unknown sync mode");
+    }
+    const void *k = kernel_ptr<T>(c);
+    if (c.smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c.smem));
+        if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+    }
+    if (c.kind == 3) {
         c.grid = 1;
         return SPTRSV_OK;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel<T>(c.sync, c.lanes),
-                                                                  c.threads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.threads, c.smem);
     if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, cudaGetErrorString(e));
-    int want = o.blocks_per_sm ? o.blocks_per_sm : std::min(per_sm, c.sync == SPTRSV_SYNC_GRID ? 1 : 4);
-    if (want > per_sm)
+    int want = o.blocks_per_sm ? o.blocks_per_sm : std::min(per_sm, c.sync == SPTRSV_SYNC_GRID ? 1 : 2);
+    if (want > per_sm || want < 1)
         return fail(SPTRSV_ERR_LAUNCH, "persistent grid of " + std::to_string(want) +
                                            " blocks/SM cannot be co-resident (max " +
                                            std::to_string(per_sm) + ")");
@@ -214,18 +275,26 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, LaunchCfg &c) {
 
 template <typename T>
 int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStream_t s) {
-    Kern<T> k = pick_kernel<T>(c.sync, c.lanes);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(c.grid);
     cfg.blockDim = dim3(c.threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = c.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = (c.sync == SPTRSV_SYNC_CTA) ? 0 : 1;   // co-residency guaranteed or error
+    attr[0].val.cooperative = (c.kind == 3) ? 0 : 1;   // co-residency guaranteed or error
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k, args);
+    cudaError_t e;
+    const int nph = int(p->h.phase_row.size()) - 1;
+    switch (c.kind) {
+        case 0: e = cudaLaunchKernelEx(&cfg, flags_kernel<T>(c.lanes), args); break;
+        case 1: e = cudaLaunchKernelEx(&cfg, walk_kernel<T, true, false>(c.lanes), args, nph, 0); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, blocks_kernel<T>(c.lanes), args); break;
+        default:
+            e = c.win ? cudaLaunchKernelEx(&cfg, walk_kernel<T, false, true>(c.lanes), args, nph, c.win)
+                      : cudaLaunchKernelEx(&cfg, walk_kernel<T, false, false>(c.lanes), args, nph, 0);
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(e == cudaErrorCooperativeLaunchTooLarge ? SPTRSV_ERR_LAUNCH : SPTRSV_ERR_CUDA,
@@ -255,7 +324,27 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *diag) {
     a.flags = p->d.flags;
     a.epoch = 0;
     a.timeout_ns = 0;
+    a.refine = 0;
+    a.sweep = 0;
+    a.x64 = nullptr;
+    a.ldx64 = 0;
+    a.rtol = 0.0;
+    a.lnorm = p->lnorm;
     return a;
+}
+
+// Device workspace owned by the plan, grown on demand (refinement vectors).
+int ensure_work(sptrsv_plan *p, size_t bytes) {
+    if (p->d.work_bytes >= bytes) return SPTRSV_OK;
+    if (p->d.work) {
+        cudaError_t e = cudaFree(p->d.work);
+        p->d.work = nullptr;
+        p->d.work_bytes = 0;
+        if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaMalloc(&p->d.work, bytes));
+    p->d.work_bytes = bytes;
+    return SPTRSV_OK;
 }
 
 int check_solve_args(const sptrsv_plan *p, const void *b, const void *x, int32_t nrhs, int64_t ld,
@@ -271,18 +360,10 @@ int check_solve_args(const sptrsv_plan *p, const void *b, const void *x, int32_t
     return SPTRSV_OK;
 }
 
-uint32_t next_epoch(sptrsv_plan *p, cudaStream_t s) {
-    if (++p->epoch == 0) {                      // wrapped: clear the flags once
-        cudaMemsetAsync(p->d.flags, 0, std::max<size_t>(size_t(p->h.n), 1) * sizeof(uint32_t), s);
-        p->epoch = 1;
-    }
-    return p->epoch;
-}
-
 template <typename T>
 int plain_solve(sptrsv_plan *p, const T *val, const T *diag, const void *b, void *x, int32_t nrhs, int64_t ld,
                 const sptrsv_solve_opts &o, cudaStream_t s, LaunchCfg &c) {
-    int st = choose<T>(p, o, c);
+    int st = choose<T>(p, o, nrhs, c);
     if (st) return st;
     SolveArgs<T> a = base_args<T>(p, val, diag);
     a.nrhs = nrhs;
@@ -290,13 +371,76 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *diag, const void *b, void
     a.x = static_cast<T *>(x);
     a.ldb = a.ldx = ld;
     a.timeout_ns = (long long)(o.timeout_s * 1e9);
-    if (c.sync == SPTRSV_SYNC_FLAGS) a.epoch = next_epoch(p, s);
+    if (c.kind == 0) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
+        CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
+    }
     // zero the counters but keep the status word: a device error of an
     // asynchronous solve stays visible until a report reads and clears it
     CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
     return launch<T>(p, c, a, s);
 }
 
+
+// FP32 sweeps with FP64 residual refinement, all decisions taken on the device:
+// for t = 0..M: r_t = b - L x_t (FP64; r_0 = b), d_t = solve32(L32, fp32(r_t)),
+// x_{t+1} = x_t + d_t (FP64, in the sweep's epilogue); then one last residual.
+// A sweep returns at once when the refinement has converged, so the whole
+// sequence is enqueued without host synchronisation.
+int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64_t ld, const sptrsv_solve_opts &o,
+                 cudaStream_t s, LaunchCfg &c) {
+    if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
+    if (o.max_iters < 0 || o.max_iters > kMaxSweeps - 2) return fail(SPTRSV_ERR_ARG, "max_iters must be in [0, 14]");
+    if (!(o.refine_tol > 0.0)) return fail(SPTRSV_ERR_ARG, "refine_tol must be positive");
+    int st = choose<float>(p, o, nrhs, c);
+    if (st) return st;
+    const int32_t n = p->h.n;
+    const size_t vec = size_t(n) * size_t(nrhs) * sizeof(float);
+    if ((st = ensure_work(p, 2 * vec + 256))) return st;
+    float *r32 = static_cast<float *>(p->d.work);
+    float *d32 = reinterpret_cast<float *>(static_cast<char *>(p->d.work) + ((vec + 255) & ~size_t(255)));
+    CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
+    ResidualArgs ra;
+    ra.n = n;
+    ra.nrhs = nrhs;
+    ra.rp = p->d.rp;
+    ra.col = p->d.col;
+    ra.hi = p->d.val_hi;
+    ra.lo = p->d.val_lo;
+    ra.dhi = p->d.diag_hi;
+    ra.dlo = p->d.diag_lo;
+    ra.perm = p->d.perm;
+    ra.b = b;
+    ra.ldb = ld;
+    ra.x = x;
+    ra.ldx = ld;
+    ra.r32 = r32;
+    ra.ctl = reinterpret_cast<Ctl *>(p->d.counters);
+    ra.dtol = o.refine_tol;
+    const int rgrid = std::max(1, std::min(4 * p->num_sms, (n + 255) / 256));
+    SolveArgs<float> a = base_args<float>(p, p->d.val_hi, p->d.diag_hi);
+    a.nrhs = nrhs;
+    a.b = r32;
+    a.ldb = n;
+    a.x = d32;
+    a.ldx = n;
+    a.timeout_ns = (long long)(o.timeout_s * 1e9);
+    a.x64 = x;
+    a.ldx64 = ld;
+    a.rtol = o.refine_tol;
+    const int M = o.max_iters;
+    for (int t = 0; t <= M + 1; ++t) {
+        ra.sweep = t;
+        k_residual<<<rgrid, 256, 0, s>>>(ra);
+        CUDA_TRY(cudaGetLastError());
+        if (t > M) break;
+        if (c.kind == 0) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));      // polled sweep: not-yet-computed
+        else CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, sizeof(unsigned long long), s));  // fresh barrier count
+        a.refine = t == 0 ? 1 : 2;
+        a.sweep = t;
+        if ((st = launch<float>(p, c, a, s))) return st;
+    }
+    return SPTRSV_OK;
+}
 
 int solve_impl(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
                const sptrsv_solve_opts &o, cudaStream_t s, LaunchCfg &c) {
@@ -306,19 +450,32 @@ int solve_impl(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld,
             if (!(p->values & SPTRSV_VALUES_F64)) return fail(SPTRSV_ERR_ARG, "plan has no FP64 values");
             return plain_solve<double>(p, p->d.val, p->d.diag, b, x, nrhs, ld, o, s, c);
         }
-        return fail(SPTRSV_ERR_ARG, "precision mode not available yet");
+        return refine_solve(p, static_cast<const double *>(b), static_cast<double *>(x), nrhs, ld, o, s, c);
     }
     if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
     return plain_solve<float>(p, p->d.val_hi, p->d.diag_hi, b, x, nrhs, ld, o, s, c);
 }
 
-int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_report *report) {
+int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_report *report, bool refine,
+                const sptrsv_solve_opts &o) {
     Ctl ctl;
     CUDA_TRY(cudaMemcpyAsync(&ctl, p->d.counters, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     std::memset(report, 0, sizeof(*report));
     report->status = ctl.status;
     report->sweeps = 1;
+    if (refine && !ctl.status) {
+        const int last = std::max(0, ctl.last_solve);
+        report->sweeps = last + 1;
+        const double xm = bits_to_d(ctl.xmax[last]);
+        report->dnorm = xm > 0 ? bits_to_d(ctl.dmax[last]) / xm : 0.0;
+        // backward error of the final iterate (residual index last + 1), if it was formed
+        const double rm = bits_to_d(ctl.rmax[last + 1]);
+        const double den = p->lnorm * xm + bits_to_d(ctl.bmax);
+        report->berr = den > 0 ? rm / den : 0.0;
+        const bool converged = ctl.done || report->dnorm <= o.refine_tol || report->berr <= o.refine_tol;
+        if (!converged) report->status = SPTRSV_ERR_NOT_CONVERGED;
+    }
     report->barriers = int64_t(ctl.barriers);
     report->flag_waits = int64_t(ctl.flag_waits);
     report->sync = c.sync;
@@ -330,6 +487,8 @@ int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_repor
         CUDA_TRY(cudaStreamSynchronize(s));
         return fail(ctl.status, "device reported " + std::string(sptrsv_status_string(ctl.status)));
     }
+    if (report->status == SPTRSV_ERR_NOT_CONVERGED)
+        return fail(SPTRSV_ERR_NOT_CONVERGED, "refinement did not converge within max_iters (x is the last iterate)");
     return SPTRSV_OK;
 }
 }  // namespace
@@ -345,7 +504,7 @@ void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
     o->lanes = 0;
     o->precision = SPTRSV_PREC_F64;
     o->max_iters = 6;
-    o->refine_tol = 1e-14;
+    o->refine_tol = 1e-13;
     o->blocks_per_sm = 0;
     o->threads = 0;
     o->timeout_s = 2.0;
@@ -368,7 +527,7 @@ int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t l
     LaunchCfg c{};
     st = solve_impl(p, b, x, nrhs, ld, dtype, o, s, c);
     if (st) return st;
-    if (report) return read_report(p, c, s, report);
+    if (report) return read_report(p, c, s, report, dtype == SPTRSV_F64 && o.precision == SPTRSV_PREC_F32_REFINE, o);
     return SPTRSV_OK;
 }
 
@@ -386,12 +545,12 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<sptrsv_solve_opts> cands;
     const bool small = int64_t(p->h.n) * nrhs <= 400000;
-    const int lane_set[] = {1, 4, 8, 32};
+    const int lane_set[] = {1, 2, 4, 8, 32};
     for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
         if (sync == SPTRSV_SYNC_CTA && !small) continue;
         for (int lanes : lane_set) {
             if (sync == SPTRSV_SYNC_CTA) {
-                for (int t : {256, 512, 1024}) {
+                for (int t : {128, 256, 512}) {
                     sptrsv_solve_opts c = o;
                     c.sync = sync; c.lanes = lanes; c.threads = t; c.blocks_per_sm = 0;
                     cands.push_back(c);
@@ -415,7 +574,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
         LaunchCfg lc{};
         if (solve_impl(p, b, x, nrhs, ld, dtype, c, s, lc)) continue;     // e.g. not co-resident
         sptrsv_report rep;
-        if (read_report(p, lc, s, &rep)) continue;
+        if (read_report(p, lc, s, &rep, dtype == SPTRSV_F64 && c.precision == SPTRSV_PREC_F32_REFINE, c)) continue;
         double t = 1e30;
         for (int rep_i = 0; rep_i < 3; ++rep_i) {
             cudaEventRecord(e0, s);

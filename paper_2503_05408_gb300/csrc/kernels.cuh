@@ -24,18 +24,28 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 #include "sptrsv.h"
 
 namespace sptrsv {
 
+constexpr int kMaxSweeps = 16;        // refinement sweeps tracked in the control block
+
 struct Ctl {                         // per-plan control block in device memory
     unsigned long long barrier;      // grid barrier arrivals (zeroed per launch)
     unsigned long long barriers;     // barriers completed (written by block 0)
-    unsigned long long flag_waits;   // flag waits that had to spin
+    unsigned long long flag_waits;   // polled gathers that had to spin
     unsigned long long cursor;       // spare work cursor
-    double norms[4];                 // refinement: max |d|, max |x|
-    int32_t status;                  // 0 or SPTRSV_ERR_*
+    // refinement, per sweep t: max |d_t|, max |x_{t+1}|, max |r_t| (non-negative
+    // doubles stored as their bit patterns, which order like unsigned integers)
+    unsigned long long dmax[kMaxSweeps], xmax[kMaxSweeps], rmax[kMaxSweeps + 1];
+    unsigned long long bmax;         // max |b|
+    int32_t done;                    // refinement converged: later kernels return at once
+    int32_t last_solve;              // index of the last FP32 sweep that ran
+    int32_t conv;                    // 1: correction test met, 2: backward-error test met
+    int32_t pad0;
+    int32_t status;                  // 0 or SPTRSV_ERR_*; kept across launches until read
     int32_t pad[7];
 };
 
@@ -57,7 +67,79 @@ struct SolveArgs {
     uint32_t *flags;
     uint32_t epoch;
     long long timeout_ns;
+    // FP32 correction sweeps of the refinement (refine != 0, T = float): the
+    // solved value is the correction d; its epilogue applies x64 += d in FP64
+    // (refine == 1: first sweep, x64 = d) and tracks max |d| and max |x64|.
+    int32_t refine, sweep;
+    double *x64;
+    int64_t ldx64;
+    double rtol, lnorm;              // backward-error test: r <= rtol * (lnorm |x| + |b|)
 };
+
+__host__ __device__ __forceinline__ double bits_to_d(unsigned long long u) {
+    double d;
+    memcpy(&d, &u, sizeof(d));
+    return d;
+}
+
+// Skip test at the start of a correction sweep: already converged, failed, or
+// the residual of the current iterate passes the backward-error test.
+template <typename T>
+__device__ __forceinline__ bool refine_skip(const SolveArgs<T> &a) {
+    if (!a.refine) return false;
+    const volatile Ctl *c = a.ctl;
+    if (c->done || c->status) return true;
+    if (a.sweep > 0) {
+        const double r = bits_to_d(c->rmax[a.sweep]);
+        const double x = bits_to_d(c->xmax[a.sweep - 1]);
+        const double b = bits_to_d(c->bmax);
+        if (r <= a.rtol * (a.lnorm * x + b)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.ctl->done = 1;
+                a.ctl->conv = 2;
+            }
+            return true;
+        }
+    }
+    return false;
+}
+
+// Epilogue of a correction: x64 += d in FP64 (lane 0 of the row's group).
+template <typename T>
+__device__ __forceinline__ void refine_apply(const SolveArgs<T> &a, int orow, int j, T d, double &dm, double &xm) {
+    double *px = a.x64 + orow + (int64_t)j * a.ldx64;
+    const double xn = (a.refine == 1 ? 0.0 : *px) + double(d);
+    *px = xn;
+    dm = fmax(dm, fabs(double(d)));
+    xm = fmax(xm, fabs(xn));
+}
+
+// Block-reduce the per-thread maxima and fold them into the sweep's slots.
+__device__ __forceinline__ void refine_flush(Ctl *ctl, int sweep, double dm, double xm) {
+    __shared__ double s_d[32], s_x[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, off));
+        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_d[w] = dm;
+        s_x[w] = xm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < nw; ++i) {
+            dm = fmax(dm, s_d[i]);
+            xm = fmax(xm, s_x[i]);
+        }
+        dm = fmax(dm, s_d[0]);
+        xm = fmax(xm, s_x[0]);
+        atomicMax(&ctl->dmax[sweep], (unsigned long long)__double_as_longlong(dm));
+        atomicMax(&ctl->xmax[sweep], (unsigned long long)__double_as_longlong(xm));
+        if (blockIdx.x == 0) ctl->last_solve = sweep;
+    }
+}
 
 __device__ __forceinline__ long long gtimer() {
     long long t;
@@ -88,20 +170,18 @@ __device__ __forceinline__ void raise_status(Ctl *c, int32_t code) { atomicCAS(&
 // timed out.
 __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned long long target, long long timeout_ns,
                                              int *s_flag) {
-    __syncthreads();
+    __syncthreads();                 // the block's writes happen-before thread 0's release
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&ctl->barrier, 1ULL);
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&ctl->barrier) : "memory");
         int ok = 1;
         const long long t0 = gtimer();
         unsigned spins = 0;
-        while (ld_acquire(&ctl->barrier) < target) {
+        while (ld_acquire(&ctl->barrier) < target) {   // acquire: later reads see every block's writes
             if ((++spins & 63u) == 1) {
                 if (ld_status(ctl) != 0) { ok = 0; break; }
                 if (gtimer() - t0 > timeout_ns) { raise_status(ctl, SPTRSV_ERR_TIMEOUT); ok = 0; break; }
             }
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();
@@ -124,7 +204,8 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
 // Eq. 2.1 for device row r: x[perm[r]] = (b[perm[r]] - sum_q val[q] x[col[q]]) / diag[r],
 // LANES lanes cooperating on the row, looping over the right-hand sides.
 template <typename T, int LANES>
-__device__ __forceinline__ void row_solve(const SolveArgs<T> &a, int r, int lane, unsigned mask) {
+__device__ __forceinline__ void row_solve(const SolveArgs<T> &a, int r, int lane, unsigned mask, double &dm,
+                                          double &xm) {
     const int beg = a.rp[r], end = a.rp[r + 1];
     const int orow = a.perm[r];
     const T dg = a.diag[r];
@@ -133,43 +214,303 @@ __device__ __forceinline__ void row_solve(const SolveArgs<T> &a, int r, int lane
         T acc = T(0);
         for (int q = beg + lane; q < end; q += LANES) acc += a.val[q] * xj[a.col[q]];
         acc = group_sum<T, LANES>(acc, mask);
-        if (lane == 0) a.x[orow + (int64_t)j * a.ldx] = (a.b[orow + (int64_t)j * a.ldb] - acc) / dg;
+        if (lane == 0) {
+            const T y = (a.b[orow + (int64_t)j * a.ldb] - acc) / dg;
+            a.x[orow + (int64_t)j * a.ldx] = y;
+            if (a.refine) refine_apply(a, orow, j, y, dm, xm);
+        }
     }
 }
 
 // Rows [r0, r1) spread over `nw` warps (this warp is `w`), 32/LANES rows per warp pass.
 template <typename T, int LANES>
-__device__ __forceinline__ void rows_span(const SolveArgs<T> &a, int r0, int r1, int w, int nw) {
+__device__ __forceinline__ void rows_span(const SolveArgs<T> &a, int r0, int r1, int w, int nw, double &dm,
+                                          double &xm) {
     constexpr int RPW = 32 / LANES;
     const int lane32 = threadIdx.x & 31;
     const int grp = lane32 / LANES, lane = lane32 % LANES;
     const unsigned mask = group_mask<LANES>(lane32);
     for (int base = r0 + w * RPW; base < r1; base += nw * RPW) {
         const int r = base + grp;
-        if (r < r1) row_solve<T, LANES>(a, r, lane, mask);
+        if (r < r1) row_solve<T, LANES>(a, r, lane, mask, dm, xm);
     }
 }
 
-template <typename T, int LANES>
-__global__ void __launch_bounds__(1024, 1) k_grid(SolveArgs<T> a) {
-    __shared__ int s_flag;
-    const int wpb = blockDim.x >> 5;
-    const int w_in_b = threadIdx.x >> 5;
-    const int gw = blockIdx.x * wpb + w_in_b;
-    const int nw = gridDim.x * wpb;
-    unsigned long long target = 0;
-    for (int s = 0; s < a.S; ++s) {
-        const int b0 = a.step_blk[s], b1 = a.step_blk[s + 1];
-        if (b1 - b0 == 1 && a.blk_phase[b0 + 1] - a.blk_phase[b0] == 1) {
-            const int q = a.blk_phase[b0];
-            rows_span<T, LANES>(a, a.phase_row[q], a.phase_row[q + 1], gw, nw);
+// ----------------------------------------------------------------------------
+// Row registers and the value-polling protocol.
+//
+// A row's structure (row pointers, original id, diagonal, right-hand side,
+// columns and values) does not depend on x, so every executor loads it ahead
+// of time into registers; only the gathers of x sit on the dependency chain.
+//
+// Ready values: before a polled solve the output x is filled with an all-ones
+// NaN (SENTINEL).  A producer publishes x[i] with one relaxed 4/8-byte store
+// (a computed value that happens to equal SENTINEL is replaced by the
+// canonical NaN), and a consumer polls x[c] itself with relaxed loads until it
+// differs from SENTINEL.  Aligned 4/8-byte accesses are single-copy atomic, so
+// the polled value IS the result: one round trip per dependency hop, no flag
+// array, no fences.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool is_sentinel(T v);
+template <>
+__device__ __forceinline__ bool is_sentinel<double>(double v) { return __double_as_longlong(v) == -1LL; }
+template <>
+__device__ __forceinline__ bool is_sentinel<float>(float v) { return __float_as_int(v) == -1; }
+
+template <typename T>
+__device__ __forceinline__ T publishable(T v) {
+    return is_sentinel(v) ? T(__int_as_float(0x7fc00000)) : v;
+}
+
+__device__ __forceinline__ double ld_poll(const double *p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_poll(const float *p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_pub(double *p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_pub(float *p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+template <typename T, int U>
+struct RowRegs {
+    int beg, end, orow;
+    T dg;
+    T b0;          // right-hand side of column 0 (lane 0), prefetched with the entries
+    int c[U];
+    T v[U];
+};
+
+template <typename T, int U>
+__device__ __forceinline__ void load_meta(const SolveArgs<T> &a, int r, RowRegs<T, U> &m) {
+    m.beg = __ldg(a.rp + r);
+    m.end = __ldg(a.rp + r + 1);
+    m.orow = __ldg(a.perm + r);
+    m.dg = __ldg(a.diag + r);
+}
+
+template <typename T, int LANES, int U>
+__device__ __forceinline__ void load_entries(const SolveArgs<T> &a, int lane, RowRegs<T, U> &m) {
+    m.b0 = (lane == 0) ? a.b[m.orow] : T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int q = m.beg + lane + u * LANES;
+        if (q < m.end) {
+            m.c[u] = __ldg(a.col + q);
+            m.v[u] = __ldg(a.val + q);
         } else {
-            for (int blk = b0 + blockIdx.x; blk < b1; blk += gridDim.x) {
-                const int q1 = a.blk_phase[blk + 1];
-                for (int q = a.blk_phase[blk]; q < q1; ++q) {
-                    rows_span<T, LANES>(a, a.phase_row[q], a.phase_row[q + 1], w_in_b, wpb);
-                    __syncthreads();
-                }
+            m.c[u] = -1;
+            m.v[u] = T(0);
+        }
+    }
+}
+
+// Spin until *p is no longer SENTINEL; bounded by the status word and the timeout.
+template <typename T>
+__device__ __noinline__ bool poll_wait(const T *p, T &v, const SolveArgs<T> &a, unsigned long long &waits) {
+    ++waits;
+    const long long t0 = gtimer();
+    unsigned spins = 0;
+    do {
+        v = ld_poll(p);
+        if (!is_sentinel(v)) return true;
+        if ((++spins & 63u) == 1) {
+            if (ld_status(a.ctl) != 0) return false;
+            if (gtimer() - t0 > a.timeout_ns) {
+                raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    } while (true);
+}
+
+// One row (Eq. 2.1) from registers.  MODE 0: gathers are plain loads (every
+// parent is finished, separated by a barrier); MODE 1: polled gathers; MODE 2:
+// gathers from the shared-memory ring `xs` (slot = original id & wmask).
+// Returns false if a bounded wait failed.
+template <typename T, int LANES, int U, int MODE>
+__device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T, U> &m, int lane,
+                                         unsigned mask, T *xs, int win, unsigned long long &waits,
+                                         double &dm, double &xm) {
+    bool ok = true;
+    for (int j = 0; j < a.nrhs; ++j) {
+        const T *xj = a.x + (int64_t)j * a.ldx;
+        const T bj = (lane != 0) ? T(0) : (j == 0 ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb]);
+        T xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (m.c[u] >= 0) {
+                if constexpr (MODE == 2) xv[u] = xs[(m.c[u] & (win - 1)) + j * win];
+                else if constexpr (MODE == 1) xv[u] = ld_poll(xj + m.c[u]);
+                else xv[u] = xj[m.c[u]];
+            } else {
+                xv[u] = T(0);
+            }
+        }
+        if constexpr (MODE == 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok && m.c[u] >= 0 && is_sentinel(xv[u])) ok = poll_wait(xj + m.c[u], xv[u], a, waits);
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += m.v[u] * xv[u];
+        // entries beyond the register tile (long rows)
+        for (int q = m.beg + lane + U * LANES; ok && q < m.end; q += LANES) {
+            const int c = __ldg(a.col + q);
+            T xc;
+            if constexpr (MODE == 2) xc = xs[(c & (win - 1)) + j * win];
+            else if constexpr (MODE == 1) {
+                xc = ld_poll(xj + c);
+                if (is_sentinel(xc)) ok = poll_wait(xj + c, xc, a, waits);
+            } else xc = xj[c];
+            acc += __ldg(a.val + q) * xc;
+        }
+        if constexpr (MODE == 1) {
+            if (!__all_sync(mask, ok)) return false;
+        }
+        acc = group_sum<T, LANES>(acc, mask);
+        if (lane == 0) {
+            const T y = (bj - acc) / m.dg;
+            T *dst = a.x + m.orow + (int64_t)j * a.ldx;
+            if constexpr (MODE == 1) st_pub(dst, publishable(y));
+            else *dst = y;
+            if constexpr (MODE == 2) xs[(m.orow & (win - 1)) + j * win] = y;
+            if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+        }
+    }
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// Polled executor (SPTRSV_SYNC_FLAGS).  Rows are dealt to groups round-robin
+// in device order and each group handles its rows in increasing order: the
+// smallest unfinished row always has finished parents and an owner at it, so
+// with every block co-resident the walk cannot deadlock.  Two-stage software
+// pipeline: metadata two rows ahead, columns/values one row ahead.
+// ----------------------------------------------------------------------------
+template <typename T, int LANES, int U>
+__global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
+    constexpr int RPW = 32 / LANES;
+    const int lane32 = threadIdx.x & 31;
+    const int grp = lane32 / LANES, lane = lane32 % LANES;
+    const unsigned mask = group_mask<LANES>(lane32);
+    const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + grp;
+    const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
+    if (refine_skip(a)) return;
+    unsigned long long waits = 0;
+    double dm = 0.0, xm = 0.0;
+    RowRegs<T, U> cur, nxt, nn;
+    int r = g;
+    if (r < a.n) {
+        load_meta(a, r, cur);
+        load_entries<T, LANES, U>(a, lane, cur);
+    }
+    if (r + G < a.n) load_meta(a, r + G, nxt);
+    for (; r < a.n; r += G) {
+        if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
+        if (r + G < a.n) load_entries<T, LANES, U>(a, lane, nxt);
+        if (!row_exec<T, LANES, U, 1>(a, cur, lane, mask, nullptr, 0, waits, dm, xm)) break;
+        cur = nxt;
+        nxt = nn;
+    }
+    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
+// ----------------------------------------------------------------------------
+// Phase walker for schedules whose supersteps are single wide phases (the
+// wavefront schedule) or, with GRID == false, any schedule walked by one
+// thread block.  GRID: rows of a phase are spread over every group of the
+// grid and a grid barrier separates phases.  CTA: rows of a phase are spread
+// over the block's groups, __syncthreads separates phases, and, when `win`
+// is non-zero, x is also kept in a shared-memory ring of `win` rows (the host
+// proved that no two rows sharing a slot are live at once).  The first row
+// each group owns in the next phase is prefetched: metadata at the start of
+// the current phase, columns/values before the barrier.
+// ----------------------------------------------------------------------------
+template <typename T, int LANES, int U, bool GRID, bool RING>
+__global__ void __launch_bounds__(512, 1) k_walk(SolveArgs<T> a, int nphases, int win) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    __shared__ int s_flag;
+    constexpr int RPW = 32 / LANES;
+    const int lane32 = threadIdx.x & 31;
+    const int grp = lane32 / LANES, lane = lane32 % LANES;
+    const unsigned mask = group_mask<LANES>(lane32);
+    const int wid = GRID ? ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) : (threadIdx.x >> 5);
+    const int g = wid * RPW + grp;
+    const int G = ((GRID ? gridDim.x * blockDim.x : blockDim.x) >> 5) * RPW;
+    if (refine_skip(a)) return;
+    unsigned long long waits = 0, target = 0;
+    double dm = 0.0, xm = 0.0;
+    RowRegs<T, U> cur, nxt;
+    int p0 = a.phase_row[0], p1 = nphases > 0 ? a.phase_row[1] : 0;
+    int p2 = nphases > 1 ? a.phase_row[2] : p1;
+    bool have = false;
+    if (nphases > 0 && p0 + g < p1) {
+        load_meta(a, p0 + g, cur);
+        load_entries<T, LANES, U>(a, lane, cur);
+        have = true;
+    }
+    for (int q = 0; q < nphases; ++q) {
+        // boundaries are loaded one phase before they gate a prefetch, off the critical path
+        const int p3 = (q + 3 <= nphases) ? __ldg(a.phase_row + q + 3) : p2;
+        const bool have_next = (q + 1 < nphases) && (p1 + g < p2);
+        if (have_next) load_meta(a, p1 + g, nxt);
+        if (have) row_exec<T, LANES, U, RING ? 2 : 0>(a, cur, lane, mask, xs, win, waits, dm, xm);
+        for (int r = p0 + g + G; r < p1; r += G) {            // rows beyond the first per group
+            RowRegs<T, U> t;
+            load_meta(a, r, t);
+            load_entries<T, LANES, U>(a, lane, t);
+            row_exec<T, LANES, U, RING ? 2 : 0>(a, t, lane, mask, xs, win, waits, dm, xm);
+        }
+        if (have_next) load_entries<T, LANES, U>(a, lane, nxt);
+        if (q + 1 < nphases) {
+            if constexpr (GRID) {
+                target += gridDim.x;
+                if (!grid_barrier(a.ctl, target, a.timeout_ns, &s_flag)) return;
+            } else {
+                __syncthreads();
+            }
+        }
+        cur = nxt;
+        have = have_next;
+        p0 = p1;
+        p1 = p2;
+        p2 = p3;
+    }
+    if (GRID && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->barriers = nphases > 0 ? nphases - 1 : 0;
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
+// Block-per-core executor for schedules whose supersteps hold several blocks
+// (GrowLocal): each block is walked by one thread block phase by phase with
+// __syncthreads, a grid barrier separates supersteps.  Kept on on-demand
+// loads: a block's rows are contiguous and its phases are short.
+template <typename T, int LANES>
+__global__ void __launch_bounds__(512, 1) k_blocks(SolveArgs<T> a) {
+    __shared__ int s_flag;
+    if (refine_skip(a)) return;
+    const int wpb = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    unsigned long long target = 0;
+    double dm = 0.0, xm = 0.0;
+    for (int s = 0; s < a.S; ++s) {
+        const int b1 = a.step_blk[s + 1];
+        for (int blk = a.step_blk[s] + blockIdx.x; blk < b1; blk += gridDim.x) {
+            const int q1 = a.blk_phase[blk + 1];
+            for (int q = a.blk_phase[blk]; q < q1; ++q) {
+                rows_span<T, LANES>(a, a.phase_row[q], a.phase_row[q + 1], w, wpb, dm, xm);
+                __syncthreads();
             }
         }
         if (s + 1 < a.S) {
@@ -178,80 +519,92 @@ __global__ void __launch_bounds__(1024, 1) k_grid(SolveArgs<T> a) {
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->barriers = a.S > 0 ? a.S - 1 : 0;
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
 }
 
-template <typename T, int LANES>
-__global__ void __launch_bounds__(1024, 1) k_cta(SolveArgs<T> a) {
-    const int wpb = blockDim.x >> 5;
-    const int w = threadIdx.x >> 5;
-    for (int s = 0; s < a.S; ++s) {
-        const int b1 = a.step_blk[s + 1];
-        for (int blk = a.step_blk[s]; blk < b1; ++blk) {
-            const int q1 = a.blk_phase[blk + 1];
-            for (int q = a.blk_phase[blk]; q < q1; ++q) {
-                rows_span<T, LANES>(a, a.phase_row[q], a.phase_row[q + 1], w, wpb);
-                __syncthreads();
+// ----------------------------------------------------------------------------
+// FP64 residual of the refinement, r = b - L x, computed from the FP32 split
+// L = hi + lo (each product formed in FP64), stored rounded to FP32 as the
+// right-hand side of the next FP32 correction sweep.  No dependencies: a plain
+// grid-stride pass over device rows.  Sweep 0 has x = 0, so r = b.  At the
+// start of sweep t >= 1 the kernel stops the refinement if the last correction
+// was small: max |d_{t-1}| <= dtol * max |x_t|.
+// ----------------------------------------------------------------------------
+struct ResidualArgs {
+    int32_t n, nrhs, sweep;
+    const int32_t *__restrict__ rp;
+    const int32_t *__restrict__ col;
+    const float *__restrict__ hi;
+    const float *__restrict__ lo;
+    const float *__restrict__ dhi;
+    const float *__restrict__ dlo;
+    const int32_t *__restrict__ perm;
+    const double *b;
+    int64_t ldb;
+    const double *x;
+    int64_t ldx;
+    float *r32;                      // n x nrhs, leading dimension n
+    Ctl *ctl;
+    double dtol;
+};
+
+static __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+    __shared__ double s_r[8], s_b[8];
+    if (a.sweep > 0) {
+        const volatile Ctl *c = a.ctl;
+        if (c->done || c->status) return;
+        const double d = bits_to_d(c->dmax[a.sweep - 1]);
+        const double x = bits_to_d(c->xmax[a.sweep - 1]);
+        if (d <= a.dtol * x) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.ctl->done = 1;
+                a.ctl->conv = 1;
             }
+            return;
         }
     }
-}
-
-// Per-row ready flags.  Rows are dealt to (warp, group) slots round-robin in
-// device order; each slot handles its rows in increasing order, so the
-// smallest unfinished row always has its parents done and its owner at it:
-// with every block co-resident the walk cannot deadlock.  Groups use their
-// own shuffle masks so one group's wait never stalls another's reduction.
-template <typename T, int LANES>
-__global__ void __launch_bounds__(1024, 1) k_flags(SolveArgs<T> a) {
-    constexpr int RPW = 32 / LANES;
-    const int wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const int nw = gridDim.x * wpb;
-    const int lane32 = threadIdx.x & 31;
-    const int grp = lane32 / LANES, lane = lane32 % LANES;
-    const unsigned mask = group_mask<LANES>(lane32);
-    unsigned long long waits = 0;
-    bool alive = true;
-    for (int base = gw * RPW; base < a.n && alive; base += nw * RPW) {
-        const int r = base + grp;
-        if (r >= a.n) break;
-        const int beg = a.rp[r], end = a.rp[r + 1];
-        // wait for this lane's parents
-        for (int q = beg + lane; q < end; q += LANES) {
-            const uint32_t *f = a.flags + a.col[q];
-            if (ld_acquire(f) != a.epoch) {
-                ++waits;
-                const long long t0 = gtimer();
-                unsigned spins = 0;
-                while (ld_acquire(f) != a.epoch) {
-                    if ((++spins & 63u) == 1) {
-                        if (ld_status(a.ctl) != 0) { alive = false; break; }
-                        if (gtimer() - t0 > a.timeout_ns) {
-                            raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
-                            alive = false;
-                            break;
-                        }
-                    }
-                }
-                if (!alive) break;
-            }
-        }
-        // all lanes of the group must agree before the reduction
-        alive = __all_sync(mask, alive);
-        if (!alive) break;
-        const int orow = a.perm[r];
-        const T dg = a.diag[r];
+    double rm = 0.0, bm = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += stride) {
+        const int o = __ldg(a.perm + r);
+        const int beg = __ldg(a.rp + r), end = __ldg(a.rp + r + 1);
+        const double dh = __ldg(a.dhi + r), dl = __ldg(a.dlo + r);
         for (int j = 0; j < a.nrhs; ++j) {
-            const T *xj = a.x + (int64_t)j * a.ldx;
-            T acc = T(0);
-            for (int q = beg + lane; q < end; q += LANES) acc += a.val[q] * xj[a.col[q]];
-            acc = group_sum<T, LANES>(acc, mask);
-            if (lane == 0) a.x[orow + (int64_t)j * a.ldx] = (a.b[orow + (int64_t)j * a.ldb] - acc) / dg;
+            double s = a.b[o + (int64_t)j * a.ldb];
+            bm = fmax(bm, fabs(s));
+            if (a.sweep > 0) {
+                const double *xj = a.x + (int64_t)j * a.ldx;
+                for (int q = beg; q < end; ++q) {
+                    const double xv = xj[__ldg(a.col + q)];
+                    s = fma(-double(__ldg(a.hi + q)), xv, s);
+                    s = fma(-double(__ldg(a.lo + q)), xv, s);
+                }
+                const double xo = xj[o];
+                s = fma(-dh, xo, s);
+                s = fma(-dl, xo, s);
+            }
+            a.r32[o + (int64_t)j * a.n] = float(s);
+            rm = fmax(rm, fabs(s));
         }
-        if (lane == 0) st_release(a.flags + orow, a.epoch);
-        __syncwarp(mask);
     }
-    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, off));
+        bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5] = rm;
+        s_b[threadIdx.x >> 5] = bm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < int(blockDim.x >> 5); ++i) {
+            rm = fmax(rm, s_r[i]);
+            bm = fmax(bm, s_b[i]);
+        }
+        atomicMax(&a.ctl->rmax[a.sweep], (unsigned long long)__double_as_longlong(rm));
+        if (a.sweep == 0) atomicMax(&a.ctl->bmax, (unsigned long long)__double_as_longlong(bm));
+    }
 }
 
 }  // namespace sptrsv

@@ -37,6 +37,9 @@ struct HostSchedule {
     std::vector<int32_t> step_blk, blk_phase, phase_row;
     int32_t max_phase_rows = 0;
     int32_t max_block_rows = 0;
+    // Smallest power-of-two ring (rows) that can hold x in shared memory when one
+    // thread block walks the phases in order (0 = none up to kMaxRingRows).
+    int32_t ring_rows = 0;
 };
 
 struct DeviceBuffers {
@@ -68,7 +71,7 @@ struct sptrsv_plan {
     int64_t nnz_off = 0;
     int64_t device_bytes = 0;
     double analyze_ms = 0.0;
-    uint32_t epoch = 0;           // ready-flag epoch, bumped per flagged sweep
+    double lnorm = 0.0;           // ||L||inf in FP64 (backward-error test of the refinement)
     int32_t sticky_status = 0;    // device error seen by an asynchronous solve
     sptrsv::DeviceBuffers d;
     // autotuner memo: best launch shape per (dtype, precision, nrhs class); the slot of the

@@ -160,3 +160,74 @@ def test_full_size_configs_f64(cfg):
     for sync in ("grid", "flags"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+# ------------------------------------------------------------ FP32 + FP64 refinement
+REFINE_CASES = {
+    "lap2d_64x64": lambda: W.laplace2d_lower(4096, 64),
+    "random_60k": lambda: W.random_window_lower(60_000, 6, 20000, 0),   # N(0,1): not FP32-exact
+    "banded_20k": lambda: W.random_window_lower(20_000, 4, 64, 1),
+    "lap3d_24": lambda: W.laplace3d_lower(24 ** 3, 24),
+    "er_30k": lambda: W.make_dominant(W.erdos_renyi_lower(30_000, 3e-4, 2)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(REFINE_CASES))
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_refine_parity(name, sync, nrhs):
+    A = REFINE_CASES[name]()
+    xs, b = W.manufactured_rhs(A, nrhs, seed=21)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    x, rep = solve_gpu(plan, b, sync=sync, precision="f32_refine")
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+    assert rep["sweeps"] >= 2            # at least one FP64-residual correction after the FP32 solve
+    assert rep["berr"] <= 1e-13
+
+
+def test_refine_needs_lo_part():
+    # The FP32 solve alone is ~1e-7 off; refinement with the hi+lo split reaches FP64 accuracy
+    # on values that FP32 cannot represent.
+    A = W.random_window_lower(50_000, 6, 20000, 3)
+    xs, b = W.manufactured_rhs(A, 1, seed=22)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    x32, _ = solve_gpu(plan, b, dtype=torch.float32, sync="flags")
+    assert 1e-9 < oracle.rel_error(x32, xo) < 1e-4
+    x, rep = solve_gpu(plan, b, sync="flags", precision="f32_refine")
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+def test_refine_not_converged_reports_and_returns_iterate():
+    A = W.random_window_lower(30_000, 6, 20000, 4)
+    xs, b = W.manufactured_rhs(A, 1, seed=23)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    bd = to_dev(b)
+    xd = torch.empty_like(bd)
+    with pytest.raises(sp.SptrsvError) as e:
+        plan.solve(bd, xd, precision="f32_refine", max_iters=0, refine_tol=1e-15)
+    assert e.value.status == sp.ERR_NOT_CONVERGED
+    torch.cuda.synchronize()
+    assert oracle.rel_error(xd.cpu().numpy(), xo) < 1e-4        # the FP32 iterate is still there
+
+
+@pytest.mark.parametrize("nrhs", [1, 32])
+def test_full_size_3d_refine(nrhs):
+    A, xs, b = W.config_3d_160(nrhs=nrhs)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    x, rep = solve_gpu(plan, b, sync="flags", precision="f32_refine")
+    assert oracle.rel_error(x, xo) <= F64_TOL
+    assert oracle.rel_error(x, xs) <= F64_TOL
+
+
+def test_full_size_random_refine():
+    A, xs, b = W.config_random_1m()
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    for sync in ("flags", "grid"):
+        x, rep = solve_gpu(plan, b, sync=sync, precision="f32_refine")
+        assert oracle.rel_error(x, xo) <= F64_TOL
