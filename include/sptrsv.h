@@ -166,6 +166,10 @@ typedef struct {
     int32_t blocks_per_sm; /* persistent grid size per SM; 0 = auto                          */
     int32_t threads;     /* threads per block; 0 = auto                                      */
     double timeout_s;    /* limit of every bounded device wait, seconds (default 2.0)         */
+    int32_t rhs_tile;    /* multi-RHS mapping: 0 = auto (lanes follow right-hand sides when
+                            nrhs >= 3), 1 = lanes split each row's entries, 4/8/16/32 = a tile of
+                            that many right-hand sides per row, each row's columns and values
+                            loaded once for the whole tile                                     */
 } sptrsv_solve_opts;
 
 void sptrsv_solve_opts_default(sptrsv_solve_opts *o);
@@ -208,6 +212,41 @@ int sptrsv_solve(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_
 int sptrsv_autotune(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_t ld,
                     int32_t dtype, const sptrsv_solve_opts *base, sptrsv_stream stream,
                     sptrsv_solve_opts *best, double *best_ms);
+
+/* -------------------------------------------------------------- batching */
+/* Many independent factors, each with its own block of right-hand sides, solved
+ * by one persistent launch replayed from a CUDA graph.  Factors are independent,
+ * so thread blocks pull (factor, RHS block of <= 32 columns) items from a queue,
+ * longest critical path first, and walk each item's supersteps alone.  In
+ * SPTRSV_PREC_F32_REFINE a block runs the item's whole refinement loop (FP32
+ * sweeps, FP64 residuals, convergence test).  With opts->sync ==
+ * SPTRSV_SYNC_AUTO the first run times the row mappings once per factor class
+ * (lanes per row or right-hand-side tile) and keeps the fastest. */
+typedef struct sptrsv_batch sptrsv_batch;
+
+/* Build a batch over `count` plans (all on one device, analysed with the value
+ * copy the precision needs); nrhs[f] right-hand sides for factor f.  dtype must
+ * be SPTRSV_F64.  opts: precision, max_iters, refine_tol, threads (per block),
+ * blocks_per_sm, sync (AUTO = autotune on first run, anything else = default
+ * mapping).  The plans must outlive the batch. */
+int sptrsv_batch_create(sptrsv_plan *const *plans, int32_t count, const int32_t *nrhs, int32_t dtype,
+                        const sptrsv_solve_opts *opts, sptrsv_batch **out);
+
+/* Run the batch: b[f], x[f] are device pointers (column-major, leading dimension
+ * ld[f] >= n_f) for factor f.  Enqueued on `stream` (the first run also captures
+ * the graph and may autotune, synchronising `stream`).  reports: NULL, or an
+ * array of `count` reports (the call then synchronises and returns the first
+ * failing factor's status, e.g. SPTRSV_ERR_NOT_CONVERGED). */
+int sptrsv_batch_run(sptrsv_batch *batch, const void *const *b, void *const *x, const int64_t *ld,
+                     sptrsv_stream stream, sptrsv_report *reports);
+
+/* Release a batch (NULL is a no-op); enqueued runs must have finished. */
+void sptrsv_batch_destroy(sptrsv_batch *batch);
+
+/* One-shot convenience: create, run once, synchronise, destroy. */
+int sptrsv_batch_solve(sptrsv_plan *const *plans, int32_t count, const void *const *b, void *const *x,
+                       const int32_t *nrhs, const int64_t *ld, int32_t dtype, const sptrsv_solve_opts *opts,
+                       sptrsv_stream stream, sptrsv_report *reports);
 
 /* --------------------------------------------------------- no allocation */
 /* Largest factor sptrsv_solve_csr_noalloc accepts (rows). */

@@ -63,7 +63,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("sync", ctypes.c_int32), ("lanes", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("rhs_tile", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -106,6 +106,15 @@ def lib():
             "sptrsv_autotune": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
                                                ctypes.POINTER(SolveOpts), ctypes.POINTER(dbl)]),
         }
+        pp = ctypes.POINTER(vp)
+        sig.update({
+            "sptrsv_batch_create": (ctypes.c_int, [pp, i32, ctypes.POINTER(i32), i32, ctypes.POINTER(SolveOpts),
+                                                   pp]),
+            "sptrsv_batch_run": (ctypes.c_int, [vp, pp, pp, ctypes.POINTER(i64), vp, ctypes.POINTER(Report)]),
+            "sptrsv_batch_destroy": (None, [vp]),
+            "sptrsv_batch_solve": (ctypes.c_int, [pp, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64), i32,
+                                                  ctypes.POINTER(SolveOpts), vp, ctypes.POINTER(Report)]),
+        })
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
@@ -219,7 +228,7 @@ class Plan:
                                      ctypes.byref(solve_opts(**base)), _stream_handle(stream),
                                      ctypes.byref(best), ctypes.byref(ms)))
         out = {"sync": best.sync, "lanes": best.lanes, "threads": best.threads,
-               "blocks_per_sm": best.blocks_per_sm}
+               "blocks_per_sm": best.blocks_per_sm, "rhs_tile": best.rhs_tile}
         self.tuned_ms = ms.value
         return out
 
@@ -264,3 +273,57 @@ class Plan:
                                 ctypes.byref(rep) if report else None)
         _check(st)
         return x, (rep.as_dict() if report else None)
+
+
+def _colmajor_info(t, n):
+    if t.dim() == 1:
+        return 1, max(n, 1)
+    if t.stride(0) != 1:
+        raise ValueError("right-hand sides must be column-major: stride (1, ld)")
+    return t.shape[1], (t.stride(1) if t.shape[1] > 1 else max(n, 1))
+
+
+class Batch:
+    """Many factors solved by one persistent launch replayed from a CUDA graph.
+
+    ``Batch(plans, nrhs, precision="f64"|"f32_refine", **opts)``; ``run(bs, xs)`` with
+    lists of CUDA float64 tensors shaped (n_f,) or (n_f, nrhs_f) column-major."""
+
+    def __init__(self, plans, nrhs, precision="f64", **opts):
+        self.plans = list(plans)
+        self.nrhs = [int(r) for r in nrhs]
+        cnt = len(self.plans)
+        arr = (ctypes.c_void_p * cnt)(*[p.handle for p in self.plans])
+        nr = (ctypes.c_int32 * cnt)(*self.nrhs)
+        o = solve_opts(precision=precision, **opts)
+        h = ctypes.c_void_p()
+        self.handle = None
+        _check(lib().sptrsv_batch_create(arr, cnt, nr, F64, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            lib().sptrsv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, bs, xs, *, stream=None, report=True):
+        cnt = len(self.plans)
+        lds = []
+        for p, b, x, r in zip(self.plans, bs, xs, self.nrhs):
+            nr, ld = _colmajor_info(b, p.n)
+            if nr != r or b.dtype.itemsize != 8 or x.shape != b.shape or x.stride() != b.stride():
+                raise ValueError("b/x must be float64 with the batch's nrhs and matching strides")
+            lds.append(ld)
+        barr = (ctypes.c_void_p * cnt)(*[b.data_ptr() for b in bs])
+        xarr = (ctypes.c_void_p * cnt)(*[x.data_ptr() for x in xs])
+        ldarr = (ctypes.c_int64 * cnt)(*lds)
+        reps = (Report * cnt)() if report else None
+        st = lib().sptrsv_batch_run(self.handle, barr, xarr, ldarr, _stream_handle(stream), reps)
+        _check(st)
+        return [r.as_dict() for r in reps] if report else None

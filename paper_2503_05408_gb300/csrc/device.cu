@@ -138,20 +138,33 @@ using Kern = void (*)(SolveArgs<T>);
 template <typename T>
 using WalkKern = void (*)(SolveArgs<T>, int, int);
 
-// Register tile per lane for each supported lanes-per-row value.
+// Register tile per lane for each supported lanes-per-row value; the
+// right-hand-side-parallel tiles (rp) keep 8 entries of every row in registers.
 constexpr int tile_for(int lanes) { return lanes == 1 ? 8 : lanes == 2 ? 4 : lanes == 4 ? 2 : 1; }
+constexpr int kRpTile = 8;
 
 bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 32; }
+bool rp_ok(int tile) { return tile == 4 || tile == 8 || tile == 16 || tile == 32; }
 
-template <typename T>
+template <typename T, bool RP>
 Kern<T> flags_kernel(int lanes) {
-    switch (lanes) {
-        case 1: return k_flags<T, 1, tile_for(1)>;
-        case 2: return k_flags<T, 2, tile_for(2)>;
-        case 4: return k_flags<T, 4, tile_for(4)>;
-        case 8: return k_flags<T, 8, tile_for(8)>;
-        case 32: return k_flags<T, 32, tile_for(32)>;
-        default: return nullptr;
+    if constexpr (RP) {
+        switch (lanes) {
+            case 4: return k_flags<T, 4, kRpTile, true>;
+            case 8: return k_flags<T, 8, kRpTile, true>;
+            case 16: return k_flags<T, 16, kRpTile, true>;
+            case 32: return k_flags<T, 32, kRpTile, true>;
+            default: return nullptr;
+        }
+    } else {
+        switch (lanes) {
+            case 1: return k_flags<T, 1, tile_for(1), false>;
+            case 2: return k_flags<T, 2, tile_for(2), false>;
+            case 4: return k_flags<T, 4, tile_for(4), false>;
+            case 8: return k_flags<T, 8, tile_for(8), false>;
+            case 32: return k_flags<T, 32, tile_for(32), false>;
+            default: return nullptr;
+        }
     }
 }
 template <typename T>
@@ -165,15 +178,25 @@ Kern<T> blocks_kernel(int lanes) {
         default: return nullptr;
     }
 }
-template <typename T, bool GRID, bool RING>
+template <typename T, bool GRID, bool RING, bool RP>
 WalkKern<T> walk_kernel(int lanes) {
-    switch (lanes) {
-        case 1: return k_walk<T, 1, tile_for(1), GRID, RING>;
-        case 2: return k_walk<T, 2, tile_for(2), GRID, RING>;
-        case 4: return k_walk<T, 4, tile_for(4), GRID, RING>;
-        case 8: return k_walk<T, 8, tile_for(8), GRID, RING>;
-        case 32: return k_walk<T, 32, tile_for(32), GRID, RING>;
-        default: return nullptr;
+    if constexpr (RP) {
+        switch (lanes) {
+            case 4: return k_walk<T, 4, kRpTile, GRID, RING, true>;
+            case 8: return k_walk<T, 8, kRpTile, GRID, RING, true>;
+            case 16: return k_walk<T, 16, kRpTile, GRID, RING, true>;
+            case 32: return k_walk<T, 32, kRpTile, GRID, RING, true>;
+            default: return nullptr;
+        }
+    } else {
+        switch (lanes) {
+            case 1: return k_walk<T, 1, tile_for(1), GRID, RING, false>;
+            case 2: return k_walk<T, 2, tile_for(2), GRID, RING, false>;
+            case 4: return k_walk<T, 4, tile_for(4), GRID, RING, false>;
+            case 8: return k_walk<T, 8, tile_for(8), GRID, RING, false>;
+            case 32: return k_walk<T, 32, tile_for(32), GRID, RING, false>;
+            default: return nullptr;
+        }
     }
 }
 
@@ -181,6 +204,7 @@ struct LaunchCfg {
     int sync, lanes, threads, grid;
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA)
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
+    bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
     size_t smem;
 };
 
@@ -204,16 +228,20 @@ int tune_slot(int32_t dtype, int32_t precision, int32_t nrhs) {
     return (dtype == SPTRSV_F32 ? 1 : 0) * 8 + (precision ? 4 : 0) + r;
 }
 
+template <typename T, bool RP>
+const void *kernel_ptr_rp(const LaunchCfg &c) {
+    switch (c.kind) {
+        case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes));
+        case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
+        case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
+        default:
+            return c.win ? reinterpret_cast<const void *>(walk_kernel<T, false, true, RP>(c.lanes))
+                         : reinterpret_cast<const void *>(walk_kernel<T, false, false, RP>(c.lanes));
+    }
+}
 template <typename T>
 const void *kernel_ptr(const LaunchCfg &c) {
-    switch (c.kind) {
-        case 0: return reinterpret_cast<const void *>(flags_kernel<T>(c.lanes));
-        case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false>(c.lanes));
-        case 2: return reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
-        default:
-            return c.win ? reinterpret_cast<const void *>(walk_kernel<T, false, true>(c.lanes))
-                         : reinterpret_cast<const void *>(walk_kernel<T, false, false>(c.lanes));
-    }
+    return c.rp ? kernel_ptr_rp<T, true>(c) : kernel_ptr_rp<T, false>(c);
 }
 
 template <typename T>
@@ -226,6 +254,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
             if (!o.lanes) o.lanes = t.lanes;
             if (!o.threads) o.threads = t.threads;
             if (!o.blocks_per_sm) o.blocks_per_sm = t.blocks_per_sm;
+            if (!o.rhs_tile) o.rhs_tile = t.rhs_tile;
         }
     }
     c.sync = o.sync;
@@ -233,15 +262,33 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         if (p->h.n <= 8192) c.sync = SPTRSV_SYNC_CTA;
         else c.sync = SPTRSV_SYNC_FLAGS;
     }
-    c.lanes = o.lanes ? o.lanes : auto_lanes(p);
-    if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
+    // multi-RHS: lanes map to right-hand sides (tile of 4..32 columns) unless rhs_tile == 1
+    int tile = o.rhs_tile;
+    if (tile == 0) {
+        tile = 1;
+        if (nrhs >= 3) {
+            tile = 4;
+            while (tile < nrhs && tile < 32) tile <<= 1;
+        }
+    }
+    c.rp = tile > 1;
+    if (c.rp) {
+        if (!rp_ok(tile)) return fail(SPTRSV_ERR_ARG, "rhs_tile must be 0, 1, 4, 8, 16 or 32");
+        c.lanes = tile;
+    } else {
+        c.lanes = o.lanes ? o.lanes : auto_lanes(p);
+        if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
+    }
     c.threads = o.threads ? o.threads : 256;
     if (c.threads < 32 || c.threads > 512 || c.threads % 32)
         return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
     c.win = 0;
     c.smem = 0;
     if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
-    else if (c.sync == SPTRSV_SYNC_GRID) c.kind = wide_phases(p) ? 1 : 2;
+    else if (c.sync == SPTRSV_SYNC_GRID) {
+        c.kind = wide_phases(p) ? 1 : 2;
+        if (c.kind == 2 && c.rp) c.rp = false, c.lanes = auto_lanes(p);   // block executor: entry lanes
+    }
     else if (c.sync == SPTRSV_SYNC_CTA) {
         c.kind = 3;
         const int w = p->h.ring_rows;
@@ -287,13 +334,12 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     cfg.numAttrs = 1;
     cudaError_t e;
     const int nph = int(p->h.phase_row.size()) - 1;
-    switch (c.kind) {
-        case 0: e = cudaLaunchKernelEx(&cfg, flags_kernel<T>(c.lanes), args); break;
-        case 1: e = cudaLaunchKernelEx(&cfg, walk_kernel<T, true, false>(c.lanes), args, nph, 0); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, blocks_kernel<T>(c.lanes), args); break;
-        default:
-            e = c.win ? cudaLaunchKernelEx(&cfg, walk_kernel<T, false, true>(c.lanes), args, nph, c.win)
-                      : cudaLaunchKernelEx(&cfg, walk_kernel<T, false, false>(c.lanes), args, nph, 0);
+    const void *k = kernel_ptr<T>(c);
+    if (c.kind == 0 || c.kind == 2) {
+        e = cudaLaunchKernelEx(&cfg, reinterpret_cast<Kern<T>>(const_cast<void *>(k)), args);
+    } else {
+        e = cudaLaunchKernelEx(&cfg, reinterpret_cast<WalkKern<T>>(const_cast<void *>(k)), args, nph,
+                               c.kind == 3 ? c.win : 0);
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -508,6 +554,7 @@ void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
     o->blocks_per_sm = 0;
     o->threads = 0;
     o->timeout_s = 2.0;
+    o->rhs_tile = 0;
 }
 
 int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
@@ -545,24 +592,23 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<sptrsv_solve_opts> cands;
     const bool small = int64_t(p->h.n) * nrhs <= 400000;
-    const int lane_set[] = {1, 2, 4, 8, 32};
+    // row mappings: (rhs_tile, lanes); entry-split lanes, plus right-hand-side tiles for nrhs >= 2
+    std::vector<std::pair<int, int>> maps;
+    for (int lanes : {1, 2, 4, 8, 32}) maps.push_back({1, lanes});
+    if (nrhs >= 2)
+        for (int tile : {4, 8, 16, 32})
+            if (tile / 2 < nrhs) maps.push_back({tile, 0});
     for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
         if (sync == SPTRSV_SYNC_CTA && !small) continue;
-        for (int lanes : lane_set) {
-            if (sync == SPTRSV_SYNC_CTA) {
-                for (int t : {128, 256, 512}) {
+        for (auto [tile, lanes] : maps) {
+            for (int t : {128, 256, 512})
+                for (int bps : {1, 2}) {
+                    if (sync == SPTRSV_SYNC_CTA && bps > 1) continue;
                     sptrsv_solve_opts c = o;
-                    c.sync = sync; c.lanes = lanes; c.threads = t; c.blocks_per_sm = 0;
+                    c.sync = sync; c.rhs_tile = tile; c.lanes = lanes; c.threads = t;
+                    c.blocks_per_sm = sync == SPTRSV_SYNC_CTA ? 0 : bps;
                     cands.push_back(c);
                 }
-            } else {
-                for (int t : {128, 256, 512})
-                    for (int bps : {1, 2}) {
-                        sptrsv_solve_opts c = o;
-                        c.sync = sync; c.lanes = lanes; c.threads = t; c.blocks_per_sm = bps;
-                        cands.push_back(c);
-                    }
-            }
         }
     }
     cudaEvent_t e0, e1;
@@ -601,6 +647,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     m.lanes = best_o.lanes;
     m.threads = best_o.threads;
     m.blocks_per_sm = best_o.blocks_per_sm;
+    m.rhs_tile = best_o.rhs_tile;
     m.ms = best_t;
     if (best) *best = best_o;
     if (best_ms) *best_ms = best_t;

@@ -297,12 +297,16 @@ __device__ __forceinline__ void load_meta(const SolveArgs<T> &a, int r, RowRegs<
     m.dg = __ldg(a.diag + r);
 }
 
-template <typename T, int LANES, int U>
+// RP (right-hand-side parallel tile): every lane of the group holds the same U
+// entries (broadcast loads) and lane l works on right-hand sides l, l+LANES, ...
+// Otherwise lanes split the row's entries and one lane owns the result.
+template <typename T, int LANES, int U, bool RP = false>
 __device__ __forceinline__ void load_entries(const SolveArgs<T> &a, int lane, RowRegs<T, U> &m) {
-    m.b0 = (lane == 0) ? a.b[m.orow] : T(0);
+    if constexpr (RP) m.b0 = (lane < a.nrhs) ? a.b[m.orow + (int64_t)lane * a.ldb] : T(0);
+    else m.b0 = (lane == 0) ? a.b[m.orow] : T(0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const int q = m.beg + lane + u * LANES;
+        const int q = RP ? m.beg + u : m.beg + lane + u * LANES;
         if (q < m.end) {
             m.c[u] = __ldg(a.col + q);
             m.v[u] = __ldg(a.val + q);
@@ -337,9 +341,59 @@ __device__ __noinline__ bool poll_wait(const T *p, T &v, const SolveArgs<T> &a, 
 // gathers from the shared-memory ring `xs` (slot = original id & wmask).
 // Returns false if a bounded wait failed.
 template <typename T, int LANES, int U, int MODE>
+__device__ __forceinline__ bool row_exec_rp(const SolveArgs<T> &a, const RowRegs<T, U> &m, int lane,
+                                            unsigned mask, T *xs, int win, unsigned long long &waits,
+                                            double &dm, double &xm) {
+    bool ok = true;
+    for (int j = lane; j < a.nrhs && ok; j += LANES) {
+        const T *xj = a.x + (int64_t)j * a.ldx;
+        const T bj = (j == lane) ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb];
+        T xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (m.c[u] >= 0) {
+                if constexpr (MODE == 2) xv[u] = xs[(m.c[u] & (win - 1)) + j * win];
+                else if constexpr (MODE == 1) xv[u] = ld_poll(xj + m.c[u]);
+                else xv[u] = xj[m.c[u]];
+            } else {
+                xv[u] = T(0);
+            }
+        }
+        if constexpr (MODE == 1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok && m.c[u] >= 0 && is_sentinel(xv[u])) ok = poll_wait(xj + m.c[u], xv[u], a, waits);
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += m.v[u] * xv[u];
+        for (int q = m.beg + U; ok && q < m.end; ++q) {
+            const int c = __ldg(a.col + q);
+            T xc;
+            if constexpr (MODE == 2) xc = xs[(c & (win - 1)) + j * win];
+            else if constexpr (MODE == 1) {
+                xc = ld_poll(xj + c);
+                if (is_sentinel(xc)) ok = poll_wait(xj + c, xc, a, waits);
+            } else xc = xj[c];
+            acc += __ldg(a.val + q) * xc;
+        }
+        if (!ok) break;
+        const T y = (bj - acc) / m.dg;
+        T *dst = a.x + m.orow + (int64_t)j * a.ldx;
+        if constexpr (MODE == 1) st_pub(dst, publishable(y));
+        else *dst = y;
+        if constexpr (MODE == 2) xs[(m.orow & (win - 1)) + j * win] = y;
+        if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+    }
+    if constexpr (MODE == 1) return __all_sync(mask, ok);
+    return true;
+}
+
+template <typename T, int LANES, int U, int MODE, bool RP = false>
 __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T, U> &m, int lane,
                                          unsigned mask, T *xs, int win, unsigned long long &waits,
                                          double &dm, double &xm) {
+    if constexpr (RP) return row_exec_rp<T, LANES, U, MODE>(a, m, lane, mask, xs, win, waits, dm, xm);
     bool ok = true;
     for (int j = 0; j < a.nrhs; ++j) {
         const T *xj = a.x + (int64_t)j * a.ldx;
@@ -397,7 +451,7 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
 // with every block co-resident the walk cannot deadlock.  Two-stage software
 // pipeline: metadata two rows ahead, columns/values one row ahead.
 // ----------------------------------------------------------------------------
-template <typename T, int LANES, int U>
+template <typename T, int LANES, int U, bool RP>
 __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
     constexpr int RPW = 32 / LANES;
     const int lane32 = threadIdx.x & 31;
@@ -412,18 +466,81 @@ __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
     int r = g;
     if (r < a.n) {
         load_meta(a, r, cur);
-        load_entries<T, LANES, U>(a, lane, cur);
+        load_entries<T, LANES, U, RP>(a, lane, cur);
     }
     if (r + G < a.n) load_meta(a, r + G, nxt);
     for (; r < a.n; r += G) {
         if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
-        if (r + G < a.n) load_entries<T, LANES, U>(a, lane, nxt);
-        if (!row_exec<T, LANES, U, 1>(a, cur, lane, mask, nullptr, 0, waits, dm, xm)) break;
+        if (r + G < a.n) load_entries<T, LANES, U, RP>(a, lane, nxt);
+        if (!row_exec<T, LANES, U, 1, RP>(a, cur, lane, mask, nullptr, 0, waits, dm, xm)) break;
         cur = nxt;
         nxt = nn;
     }
     if (waits) atomicAdd(&a.ctl->flag_waits, waits);
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
+// ----------------------------------------------------------------------------
+// One thread block walks every phase of a factor (phases separated by
+// __syncthreads).  Shared by the single-block executor and the batched
+// executor, where each block walks one independent factor.  Same pipeline as
+// the grid walker: e0 executes, m1's entries and m2's metadata are in flight.
+// ----------------------------------------------------------------------------
+template <typename T, int LANES, int U, bool RING, bool RP>
+__device__ __forceinline__ void walk_block(const SolveArgs<T> &a, int nphases, int win, T *xs, double &dm,
+                                           double &xm) {
+    constexpr int RPW = 32 / LANES;
+    constexpr int MODE = RING ? 2 : 0;
+    const int lane32 = threadIdx.x & 31;
+    const int grp = lane32 / LANES, lane = lane32 % LANES;
+    const unsigned mask = group_mask<LANES>(lane32);
+    const int g = (threadIdx.x >> 5) * RPW + grp;
+    const int G = (blockDim.x >> 5) * RPW;
+    unsigned long long waits = 0;
+    auto bound = [&](int i) { return i <= nphases ? __ldg(a.phase_row + i) : a.phase_row[nphases]; };
+    int pb0 = bound(0), pb1 = bound(1), pb2 = bound(2), pb3 = bound(3);
+    RowRegs<T, U> e0, m1, m2;
+    bool h0 = nphases > 0 && pb0 + g < pb1;
+    bool h1 = nphases > 1 && pb1 + g < pb2;
+    if (h0) {
+        load_meta(a, pb0 + g, e0);
+        load_entries<T, LANES, U, RP>(a, lane, e0);
+    }
+    if (h1) load_meta(a, pb1 + g, m1);
+    for (int q = 0; q < nphases; ++q) {
+        const int pb4 = bound(q + 4);
+        const bool h2 = (q + 2 < nphases) && (pb2 + g < pb3);
+        if (h2) load_meta(a, pb2 + g, m2);
+        if (h1) load_entries<T, LANES, U, RP>(a, lane, m1);
+        if (h0) row_exec<T, LANES, U, MODE, RP>(a, e0, lane, mask, xs, win, waits, dm, xm);
+        for (int r = pb0 + g + G; r < pb1; r += G) {
+            RowRegs<T, U> t;
+            load_meta(a, r, t);
+            load_entries<T, LANES, U, RP>(a, lane, t);
+            row_exec<T, LANES, U, MODE, RP>(a, t, lane, mask, xs, win, waits, dm, xm);
+        }
+        __syncthreads();
+        e0 = m1;
+        h0 = h1;
+        m1 = m2;
+        h1 = h2;
+        pb0 = pb1;
+        pb1 = pb2;
+        pb2 = pb3;
+        pb3 = pb4;
+    }
+}
+
+// Maximum over the thread block (every thread gets the result).
+__device__ __forceinline__ double block_max(double v, double *s_scratch) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = s_scratch[0];
+    for (int i = 1; i < int(blockDim.x >> 5); ++i) v = fmax(v, s_scratch[i]);
+    return v;
 }
 
 // ----------------------------------------------------------------------------
@@ -437,43 +554,49 @@ __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
 // each group owns in the next phase is prefetched: metadata at the start of
 // the current phase, columns/values before the barrier.
 // ----------------------------------------------------------------------------
-template <typename T, int LANES, int U, bool GRID, bool RING>
+template <typename T, int LANES, int U, bool GRID, bool RING, bool RP>
 __global__ void __launch_bounds__(512, 1) k_walk(SolveArgs<T> a, int nphases, int win) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
     __shared__ int s_flag;
+    if (refine_skip(a)) return;
     constexpr int RPW = 32 / LANES;
+    constexpr int MODE = RING ? 2 : 0;
     const int lane32 = threadIdx.x & 31;
     const int grp = lane32 / LANES, lane = lane32 % LANES;
     const unsigned mask = group_mask<LANES>(lane32);
     const int wid = GRID ? ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) : (threadIdx.x >> 5);
     const int g = wid * RPW + grp;
     const int G = ((GRID ? gridDim.x * blockDim.x : blockDim.x) >> 5) * RPW;
-    if (refine_skip(a)) return;
     unsigned long long waits = 0, target = 0;
     double dm = 0.0, xm = 0.0;
-    RowRegs<T, U> cur, nxt;
-    int p0 = a.phase_row[0], p1 = nphases > 0 ? a.phase_row[1] : 0;
-    int p2 = nphases > 1 ? a.phase_row[2] : p1;
-    bool have = false;
-    if (nphases > 0 && p0 + g < p1) {
-        load_meta(a, p0 + g, cur);
-        load_entries<T, LANES, U>(a, lane, cur);
-        have = true;
+    // Three-stage pipeline over this group's first row of each phase:
+    //   e0 - phase q:   entries in registers, executed now
+    //   m1 - phase q+1: metadata arrived; its entries are requested during phase q
+    //   m2 - phase q+2: metadata requested during phase q
+    // Phase boundaries run one phase further ahead (pb3 is known at phase q).
+    auto bound = [&](int i) { return i <= nphases ? __ldg(a.phase_row + i) : a.phase_row[nphases]; };
+    int pb0 = bound(0), pb1 = bound(1), pb2 = bound(2), pb3 = bound(3);
+    RowRegs<T, U> e0, m1, m2;
+    bool h0 = nphases > 0 && pb0 + g < pb1;
+    bool h1 = nphases > 1 && pb1 + g < pb2;
+    if (h0) {
+        load_meta(a, pb0 + g, e0);
+        load_entries<T, LANES, U, RP>(a, lane, e0);
     }
+    if (h1) load_meta(a, pb1 + g, m1);
     for (int q = 0; q < nphases; ++q) {
-        // boundaries are loaded one phase before they gate a prefetch, off the critical path
-        const int p3 = (q + 3 <= nphases) ? __ldg(a.phase_row + q + 3) : p2;
-        const bool have_next = (q + 1 < nphases) && (p1 + g < p2);
-        if (have_next) load_meta(a, p1 + g, nxt);
-        if (have) row_exec<T, LANES, U, RING ? 2 : 0>(a, cur, lane, mask, xs, win, waits, dm, xm);
-        for (int r = p0 + g + G; r < p1; r += G) {            // rows beyond the first per group
+        const int pb4 = bound(q + 4);
+        const bool h2 = (q + 2 < nphases) && (pb2 + g < pb3);
+        if (h2) load_meta(a, pb2 + g, m2);
+        if (h1) load_entries<T, LANES, U, RP>(a, lane, m1);
+        if (h0) row_exec<T, LANES, U, MODE, RP>(a, e0, lane, mask, xs, win, waits, dm, xm);
+        for (int r = pb0 + g + G; r < pb1; r += G) {          // rows beyond the first per group
             RowRegs<T, U> t;
             load_meta(a, r, t);
-            load_entries<T, LANES, U>(a, lane, t);
-            row_exec<T, LANES, U, RING ? 2 : 0>(a, t, lane, mask, xs, win, waits, dm, xm);
+            load_entries<T, LANES, U, RP>(a, lane, t);
+            row_exec<T, LANES, U, MODE, RP>(a, t, lane, mask, xs, win, waits, dm, xm);
         }
-        if (have_next) load_entries<T, LANES, U>(a, lane, nxt);
         if (q + 1 < nphases) {
             if constexpr (GRID) {
                 target += gridDim.x;
@@ -482,11 +605,14 @@ __global__ void __launch_bounds__(512, 1) k_walk(SolveArgs<T> a, int nphases, in
                 __syncthreads();
             }
         }
-        cur = nxt;
-        have = have_next;
-        p0 = p1;
-        p1 = p2;
-        p2 = p3;
+        e0 = m1;
+        h0 = h1;
+        m1 = m2;
+        h1 = h2;
+        pb0 = pb1;
+        pb1 = pb2;
+        pb2 = pb3;
+        pb3 = pb4;
     }
     if (GRID && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->barriers = nphases > 0 ? nphases - 1 : 0;
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);

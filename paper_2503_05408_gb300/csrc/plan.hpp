@@ -78,7 +78,7 @@ struct sptrsv_plan {
     // call being served is selected by sptrsv_solve before it picks a configuration
     struct TunedCfg {
         bool valid = false;
-        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0;
+        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0, rhs_tile = 0;
         double ms = 0.0;
     };
     TunedCfg tuned[16];

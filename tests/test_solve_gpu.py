@@ -90,14 +90,26 @@ def test_f64_growlocal_parity(name, sync, k):
 
 
 @pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
-@pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0)])
-def test_multi_rhs(sync, nrhs, ld_pad):
+@pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0), (37, 3)])
+@pytest.mark.parametrize("rhs_tile", [0, 1, 4, 32])
+def test_multi_rhs(sync, nrhs, ld_pad, rhs_tile):
     A = W.laplace3d_lower(20 ** 3, 20)
     xs, b = W.manufactured_rhs(A, nrhs, seed=13)
     xo = oracle.solve(A, b)
     plan = sp.Plan(A)
-    x, rep = solve_gpu(plan, b, ld=A.n + ld_pad, sync=sync, lanes=1)
+    x, rep = solve_gpu(plan, b, ld=A.n + ld_pad, sync=sync, lanes=1, rhs_tile=rhs_tile)
     assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("rhs_tile", [1, 8])
+def test_multi_rhs_random_rows(sync, rhs_tile):
+    # rows longer than the 8-entry register tile exercise the on-demand tail
+    A = W.random_window_lower(8_000, 12, 400, 6)
+    xs, b = W.manufactured_rhs(A, 8, seed=16)
+    plan = sp.Plan(A)
+    x, rep = solve_gpu(plan, b, sync=sync, rhs_tile=rhs_tile)
+    assert oracle.rel_error(x, oracle.solve(A, b)) <= F64_TOL
 
 
 def test_f32_solve():
