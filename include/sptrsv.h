@@ -248,6 +248,63 @@ int sptrsv_batch_solve(sptrsv_plan *const *plans, int32_t count, const void *con
                        const int32_t *nrhs, const int64_t *ld, int32_t dtype, const sptrsv_solve_opts *opts,
                        sptrsv_stream stream, sptrsv_report *reports);
 
+/* --------------------------------------------------------------- serving */
+/* Continuous batching over resident factors.  A dispatcher thread admits
+ * submitted requests in arrival order as soon as their device workspace fits
+ * the HBM budget left by the registered factors, packs all admitted requests
+ * into one launch of the batched executor on a free stream slot and keeps
+ * admitting while earlier launches run, so requests that arrive while others
+ * are on the GPU overlap with them.  Each request's result does not depend on
+ * what it was batched with (it is computed by one thread block alone).
+ * SPTRSV_SERVE_SERIAL_F64 serves the same stream the plain way - one request
+ * per FP64 sptrsv_solve launch, one stream, arrival order - as a baseline with
+ * identical bookkeeping. */
+typedef struct sptrsv_server sptrsv_server;
+enum { SPTRSV_SERVE_CONTINUOUS = 0, SPTRSV_SERVE_SERIAL_F64 = 1 };
+
+typedef struct {
+    int32_t mode;        /* SPTRSV_SERVE_*                                                  */
+    int32_t streams;     /* concurrent launches in flight (8)                               */
+    int32_t max_batch;   /* requests packed into one launch at most (256)                   */
+    int32_t precision;   /* continuous mode: SPTRSV_PREC_F32_REFINE (default) or _F64       */
+    int32_t max_iters;   /* refinement limits, as in sptrsv_solve_opts (6, 1e-13)           */
+    double refine_tol;
+    int32_t threads;     /* threads per block of the batched executor (256)                 */
+    int32_t device;      /* CUDA device (0)                                                 */
+} sptrsv_serve_opts;
+
+typedef struct {
+    int64_t submitted, completed, rejected, launches;
+    double mean_batch;              /* requests per launch                                  */
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* latency = completion - submission          */
+    double solves_per_s;            /* completed / (last completion - first submission)     */
+    int64_t peak_workspace_bytes, arena_bytes, factor_bytes;
+} sptrsv_serve_statistics;
+
+void sptrsv_serve_opts_default(sptrsv_serve_opts *o);
+/* Create a server with an HBM budget (bytes) for resident factors + request workspace.
+ * Starts the dispatcher thread.  The workspace arena (budget minus factor bytes) is
+ * allocated by the first submit. */
+int sptrsv_serve_create(size_t hbm_budget, const sptrsv_serve_opts *opts, sptrsv_server **out);
+/* Make an analysed plan resident (it must outlive the server); BUDGET if it does not fit.
+ * All factors must be registered before the first submit. */
+int sptrsv_serve_register(sptrsv_server *server, sptrsv_plan *plan, int32_t *factor_id);
+/* Submit L_f x = b for nrhs right-hand sides: b, x are caller-owned device pointers
+ * (column-major, leading dimension ld) that must stay valid until the request completes.
+ * Returns at once with req_id; BUDGET if the request could never fit the budget. */
+int sptrsv_serve_submit(sptrsv_server *server, int32_t factor_id, const double *b, double *x,
+                        int32_t nrhs, int64_t ld, uint64_t *req_id);
+/* PENDING until the request finished; then fills `out`, forgets the request and returns its
+ * status (0, or e.g. SPTRSV_ERR_NOT_CONVERGED). */
+int sptrsv_serve_poll(sptrsv_server *server, uint64_t req_id, sptrsv_report *out);
+/* As poll, blocking up to timeout_s seconds (PENDING on timeout). */
+int sptrsv_serve_wait(sptrsv_server *server, uint64_t req_id, double timeout_s, sptrsv_report *out);
+/* Block until every submitted request has completed (PENDING on timeout). */
+int sptrsv_serve_drain(sptrsv_server *server, double timeout_s);
+int sptrsv_serve_stats(sptrsv_server *server, sptrsv_serve_statistics *out);
+/* Stop the dispatcher, wait for in-flight launches, free the server (NULL: no-op). */
+void sptrsv_serve_destroy(sptrsv_server *server);
+
 /* --------------------------------------------------------- no allocation */
 /* Largest factor sptrsv_solve_csr_noalloc accepts (rows). */
 #define SPTRSV_NOALLOC_MAX_ROWS (1 << 20)

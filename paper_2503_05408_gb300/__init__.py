@@ -78,6 +78,22 @@ class Report(ctypes.Structure):
         return d
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double),
+                ("threads", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("peak_workspace_bytes", ctypes.c_int64),
+                ("arena_bytes", ctypes.c_int64), ("factor_bytes", ctypes.c_int64)]
+
+
+SERVE_CONTINUOUS, SERVE_SERIAL_F64 = 0, 1
+
 _lib = None
 
 
@@ -114,6 +130,17 @@ def lib():
             "sptrsv_batch_destroy": (None, [vp]),
             "sptrsv_batch_solve": (ctypes.c_int, [pp, i32, pp, pp, ctypes.POINTER(i32), ctypes.POINTER(i64), i32,
                                                   ctypes.POINTER(SolveOpts), vp, ctypes.POINTER(Report)]),
+        })
+        sig.update({
+            "sptrsv_serve_opts_default": (None, [ctypes.POINTER(ServeOpts)]),
+            "sptrsv_serve_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ServeOpts), pp]),
+            "sptrsv_serve_register": (ctypes.c_int, [vp, vp, ctypes.POINTER(i32)]),
+            "sptrsv_serve_submit": (ctypes.c_int, [vp, i32, vp, vp, i32, i64, ctypes.POINTER(ctypes.c_uint64)]),
+            "sptrsv_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(Report)]),
+            "sptrsv_serve_wait": (ctypes.c_int, [vp, ctypes.c_uint64, dbl, ctypes.POINTER(Report)]),
+            "sptrsv_serve_drain": (ctypes.c_int, [vp, dbl]),
+            "sptrsv_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServeStats)]),
+            "sptrsv_serve_destroy": (None, [vp]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -327,3 +354,68 @@ class Batch:
         st = lib().sptrsv_batch_run(self.handle, barr, xarr, ldarr, _stream_handle(stream), reps)
         _check(st)
         return [r.as_dict() for r in reps] if report else None
+
+
+class Server:
+    """Continuous-batching server over resident plans (see include/sptrsv.h)."""
+
+    def __init__(self, budget_bytes, mode="continuous", precision="f32_refine", device=0, **kw):
+        o = ServeOpts()
+        lib().sptrsv_serve_opts_default(ctypes.byref(o))
+        o.mode = SERVE_CONTINUOUS if mode == "continuous" else SERVE_SERIAL_F64
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.device = int(device)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        self.handle = None
+        _check(lib().sptrsv_serve_create(int(budget_bytes), ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self.plans = []
+
+    def register(self, plan):
+        fid = ctypes.c_int32()
+        _check(lib().sptrsv_serve_register(self.handle, plan.handle, ctypes.byref(fid)))
+        self.plans.append(plan)
+        return fid.value
+
+    def submit(self, fid, b, x):
+        nrhs, ld = _colmajor_info(b, self.plans[fid].n)
+        rid = ctypes.c_uint64()
+        _check(lib().sptrsv_serve_submit(self.handle, int(fid), b.data_ptr(), x.data_ptr(), nrhs, ld,
+                                         ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid):
+        """None while pending, else the report dict (raises on a failed request)."""
+        rep = Report()
+        st = lib().sptrsv_serve_poll(self.handle, ctypes.c_uint64(rid), ctypes.byref(rep))
+        if st == ERR_PENDING:
+            return None
+        _check(st)
+        return rep.as_dict()
+
+    def wait(self, rid, timeout=60.0):
+        rep = Report()
+        st = lib().sptrsv_serve_wait(self.handle, ctypes.c_uint64(rid), float(timeout), ctypes.byref(rep))
+        _check(st)
+        return rep.as_dict()
+
+    def drain(self, timeout=600.0):
+        _check(lib().sptrsv_serve_drain(self.handle, float(timeout)))
+
+    def stats(self):
+        s = ServeStats()
+        _check(lib().sptrsv_serve_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().sptrsv_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

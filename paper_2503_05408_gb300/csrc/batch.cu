@@ -19,6 +19,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "plan.hpp"
 
@@ -34,36 +35,6 @@ namespace {
                         std::string(#expr) + ": " + cudaGetErrorString(e_));             \
         }                                                                                \
     } while (0)
-
-// Row mappings a block can use for an item (variant id -> kernel shape).
-enum Variant : int32_t {
-    V_L1 = 0, V_L2, V_L4,              // lanes split each row's entries
-    V_T4, V_T8, V_T16, V_T32,          // right-hand-side tiles
-    V_COUNT
-};
-constexpr int kVariantLanes[V_COUNT] = {1, 2, 4, 4, 8, 16, 32};
-
-struct BatchItem {
-    int32_t n, nphases, win, variant, nrhs;
-    const int32_t *rp, *col, *perm, *phase_row;
-    const double *val, *diag;                       // FP64 values
-    const float *hi, *lo, *dhi, *dlo;               // FP32 split
-    double lnorm;
-    const void *b;
-    void *x;
-    int64_t ldb, ldx;
-    float *r32, *d32;                               // refinement workspace, leading dimension n
-};
-
-struct ItemResult {
-    int32_t status, sweeps;
-    double dnorm, berr;
-};
-
-struct BatchCfg {
-    int32_t refine, max_iters;
-    double tol;
-};
 
 template <typename T>
 __device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *val, const T *diag) {
@@ -220,6 +191,30 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
 }
 
 }  // namespace
+
+int batch_occupancy(int threads, size_t smem, int *per_sm) {
+    if (smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch, threads, smem);
+    if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, cudaGetErrorString(e));
+    return SPTRSV_OK;
+}
+
+int batch_launch(const BatchItem *d_items, int count, ItemResult *d_res, unsigned int *d_cursor,
+                 const BatchCfg &cfg, int grid, int threads, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_cursor, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        k_batch<<<grid, threads, smem, s>>>(d_items, count, d_res, d_cursor, cfg);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    return SPTRSV_OK;
+}
+
+namespace {
+}  // namespace
 }  // namespace sptrsv
 
 using namespace sptrsv;
@@ -249,7 +244,7 @@ struct sptrsv_batch {
 namespace sptrsv {
 namespace {
 
-int default_variant(const sptrsv_plan *p, int nrhs) {
+int default_variant_impl(const sptrsv_plan *p, int nrhs) {
     if (nrhs >= 3) return nrhs <= 4 ? V_T4 : nrhs <= 8 ? V_T8 : nrhs <= 16 ? V_T16 : V_T32;
     const double per_row = p->h.n ? double(p->nnz_off) / p->h.n : 0.0;
     return per_row <= 8.0 ? V_L1 : per_row <= 16.0 ? V_L2 : V_L4;
@@ -262,6 +257,31 @@ int item_win(const sptrsv_plan *p, int nrhs, size_t elem, size_t budget) {
 }
 
 constexpr size_t kBatchRingBudget = 64 * 1024;     // per block: leaves room for 2-3 blocks per SM
+}  // namespace
+
+int batch_default_variant(const sptrsv_plan *p, int nrhs) { return default_variant_impl(p, nrhs); }
+
+void batch_fill_item(BatchItem &it, const sptrsv_plan *p, int nrhs, bool refine, size_t ring_budget) {
+    it = BatchItem{};
+    it.n = p->h.n;
+    it.nphases = int32_t(p->h.phase_row.size()) - 1;
+    it.nrhs = nrhs;
+    it.win = item_win(p, nrhs, refine ? sizeof(float) : sizeof(double), ring_budget);
+    it.variant = default_variant_impl(p, nrhs);
+    it.rp = p->d.rp;
+    it.col = p->d.col;
+    it.perm = p->d.perm;
+    it.phase_row = p->d.phase_row;
+    it.val = p->d.val;
+    it.diag = p->d.diag;
+    it.hi = p->d.val_hi;
+    it.lo = p->d.val_lo;
+    it.dhi = p->d.diag_hi;
+    it.dlo = p->d.diag_lo;
+    it.lnorm = p->lnorm;
+}
+
+namespace {
 
 int build_graph(sptrsv_batch *B) {
     if (B->exec) return SPTRSV_OK;
@@ -427,7 +447,7 @@ int sptrsv_batch_create(sptrsv_plan *const *plans, int32_t count, const int32_t 
             it.nphases = int32_t(p->h.phase_row.size()) - 1;
             it.nrhs = std::min(32, nrhs[f] - c0);
             it.win = item_win(p, it.nrhs, elem, kBatchRingBudget);
-            it.variant = default_variant(p, it.nrhs);
+            it.variant = default_variant_impl(p, it.nrhs);
             it.rp = p->d.rp;
             it.col = p->d.col;
             it.perm = p->d.perm;

@@ -25,7 +25,8 @@ def test_library_exports_every_declared_symbol(L):
     import re
     import os
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "sptrsv.h")).read()
-    names = set(re.findall(r"\b(sptrsv_[a-z_0-9]+)\s*\(", hdr))
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)                     # drop comments
+    names = set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(sptrsv_[a-z_0-9]+)\s*\(", hdr, re.M))
     assert names, "no declarations found"
     for name in sorted(names):
         assert hasattr(L, name), f"{name} declared in include/sptrsv.h but not exported"
