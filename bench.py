@@ -51,7 +51,16 @@ WORKLOADS = {
                           desc="lower triangle of the 7-point Laplacian on 160^3, FP64, 1 RHS"),
     "lap2d_64_f64": dict(make=W.config_small_2d, dtype="f64", nrhs=1,
                          desc="lower triangle of the 5-point Laplacian on 64x64, FP64, 1 RHS"),
+    "lap3d_160_refine_r1": dict(make=W.config_3d_160, dtype="f32+f64-refine", nrhs=1, precision="f32_refine",
+                                desc="7-point Laplacian 160^3, FP32 sweeps + FP64 residual refinement, 1 RHS"),
+    "lap3d_160_refine_r32": dict(make=lambda: W.config_3d_160(nrhs=32), dtype="f32+f64-refine", nrhs=32,
+                                 precision="f32_refine",
+                                 desc="7-point Laplacian 160^3, FP32 sweeps + FP64 residual refinement, "
+                                      "32 RHS column-major"),
+    "lap3d_160_f64_r32": dict(make=lambda: W.config_3d_160(nrhs=32), dtype="f64", nrhs=32,
+                              desc="7-point Laplacian 160^3, FP64, 32 RHS column-major"),
 }
+SPECIAL = ("batch_256x8", "serve_10k")
 
 
 def parse_args():
@@ -60,7 +69,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random_1m_f64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(SPECIAL), default="random_1m_f64")
+    ap.add_argument("--precision", default=None, help="f64 or f32_refine (batch / single workloads)")
+    ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--baseline-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-baseline-requests", type=int, default=400)
     ap.add_argument("--sync", default=None)
     ap.add_argument("--lanes", type=int, default=None)
     ap.add_argument("--threads", type=int, default=None)
@@ -244,12 +257,17 @@ def run_ours(args):
     st = plan.stats()
 
     tdtype = torch.float64
-    b = torch.from_numpy(np.ascontiguousarray(b_np[:, 0])).to(f"cuda:{local}", tdtype)
-    x = torch.empty_like(b)
+    if nrhs == 1:
+        b = torch.from_numpy(np.ascontiguousarray(b_np[:, 0])).to(f"cuda:{local}", tdtype)
+    else:
+        b = torch.from_numpy(np.ascontiguousarray(b_np.T)).to(f"cuda:{local}", tdtype).T
+    x = torch.empty_strided(b.shape, b.stride(), dtype=tdtype, device=b.device)
+    precision = args.precision or spec.get("precision", "f64")
     opts = dict(sync=args.sync, lanes=args.lanes, threads=args.threads, blocks_per_sm=args.blocks_per_sm)
     opts = {k: v for k, v in opts.items() if v is not None}
+    opts["precision"] = precision
     if "sync" not in opts:
-        opts.update(plan.autotune(b, x))
+        opts.update(plan.autotune(b, x, precision=precision))
     _, rep = plan.solve(b, x, **opts)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
@@ -280,10 +298,10 @@ def run_ours(args):
     dev_total = sum(durs)
 
     # end to end through the public API with host buffers
-    b_host = torch.from_numpy(np.ascontiguousarray(b_np[:, 0])).to(tdtype).pin_memory()
-    x_host = torch.empty_like(b_host).pin_memory()
-    b2 = torch.empty_like(b)
-    x2 = torch.empty_like(b)
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty_strided(b.shape, b.stride(), dtype=tdtype).pin_memory()
+    b2 = torch.empty_strided(b.shape, b.stride(), dtype=tdtype, device=b.device)
+    x2 = torch.empty_strided(b.shape, b.stride(), dtype=tdtype, device=b.device)
     for _ in range(args.warmup):
         b2.copy_(b_host, non_blocking=True)
         plan.solve(b2, x2, report=False, **opts)
@@ -312,7 +330,9 @@ def run_ours(args):
     value = nnz_step * args.steps * world / dev_total
     e2e_value = nnz_step * args.steps * world / e2e_total
     mean_s = dev_total / args.steps
-    bytes_launch = algorithmic_bytes(A.n, A.nnz, nrhs, 8)
+    # HBM bytes of one sweep: FP64 values for a plain solve, FP32 values (hi) for a refinement sweep
+    bytes_launch = algorithmic_bytes(A.n, A.nnz, nrhs, 8 if precision == "f64" else 4,
+                                     x_bytes=8 if precision == "f64" else 4)
     peak, peak_src = measured_peaks()
     achieved = bytes_launch / mean_s / 1e9
     kernel_tag = f"solve_{SYNC_TAG.get(rep['sync_name'], rep['sync_name'])}_{args.workload}"
@@ -333,16 +353,24 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": bytes_launch},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
                 "d2h_bytes_per_step": int(x_host.numel() * 8)},
-        "gpu_launches": args.steps,
+        # refinement: 8 residual + 7 sweep launches per solve at the default max_iters = 6
+        "gpu_launches": args.steps * (1 if precision == "f64" else 15),
         "clocks": clk,
         "sync_points_per_step": rep["barriers"] + rep["flag_waits"],
         "analyze_ms": analyze_s * 1e3,
+        "precision": precision,
+        "refine_sweeps": rep["sweeps"],
     }
+    if precision != "f64":
+        line["roofline"]["note"] = ("dominant kernel = one FP32 sweep; achieved uses the mean time of the whole "
+                                    "refined solve over sweeps x sweep bytes")
+        line["roofline"]["achieved"] = bytes_launch * rep["sweeps"] / mean_s / 1e9
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
     if rank == 0 and not args.no_cpu_baseline:
-        cpu, x_or, cpu_s = cpu_oracle_leg(A, b_np, args.cpu_seconds)
+        cpu, x_or, cpu_s = cpu_oracle_leg(A, b_np, args.cpu_seconds, max_solves=None if nrhs == 1 else 3)
         line["cpu_baseline"] = cpu
         import oracle
-        line["err_vs_oracle"] = oracle.rel_error(x.double().cpu().numpy(), x_or)
+        line["err_vs_oracle"] = oracle.rel_error(x.double().cpu().numpy().reshape(A.n, -1), x_or)
         gain = cpu_s - mean_s
         line["amortization"] = (analyze_s / gain) if gain > 0 else None   # Eq. 7.1
     if rank == 0:
@@ -352,11 +380,283 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched workload
+def _colmajor_dev(b_np, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(b_np.T)).to(dev).T
+
+
+def run_batch(args):
+    """256 independent factors (log-uniform n in [1k, 50k], 2D / 3D / banded), 8 RHS each,
+    one persistent launch per step replayed from a CUDA graph; compared with one plain
+    FP64 sptrsv_solve launch per factor on one stream."""
+    import torch
+
+    import paper_2503_05408_gb300 as sp
+    world, rank, local = dist_info()
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    count = 256
+    factors = [W.batch_factor(f) for f in range(count)]
+    nrhs = 8
+    rhs = [W.manufactured_rhs(A, nrhs, seed=7000 + i) for i, A in enumerate(factors)]
+    plans = [sp.Plan(A, device=local) for A in factors]
+    bs = [_colmajor_dev(b, dev) for _, b in rhs]
+    xs = [torch.empty_strided(b.shape, b.stride(), dtype=torch.float64, device=dev) for b in bs]
+    precision = args.precision or "f32_refine"
+    batch = sp.Batch(plans, [nrhs] * count, precision=precision)
+    reps = batch.run(bs, xs)                        # first run: autotune + graph capture
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        batch.run(bs, xs, report=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        batch.run(bs, xs, report=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_batch = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3 / args.steps
+    # comparison: plain FP64, one launch per factor, one stream
+    xs2 = [torch.empty_like(x) for x in xs]
+    for p, b, x in zip(plans, bs, xs2):
+        p.solve(b, x, report=False, precision="f64")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps_plain = 3
+    e0.record(stream)
+    for _ in range(reps_plain):
+        for p, b, x in zip(plans, bs, xs2):
+            p.solve(b, x, report=False, precision="f64")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3 / reps_plain
+    nnz = sum(A.nnz for A in factors) * nrhs
+    n_tot = sum(A.n for A in factors)
+    bytes_step = sum(algorithmic_bytes(A.n, A.nnz, nrhs, 4 if precision != "f64" else 8,
+                                       x_bytes=8) for A in factors)
+    peak, peak_src = measured_peaks()
+    line = {"metric": METRIC, "value": nnz * world / t_batch, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64-refine" if precision != "f64" else "f64",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": "batch_256x8", "factors": count, "nrhs": nrhs, "sum_n": n_tot,
+                       "sum_nnz": nnz // nrhs, "l2": "flushed between steps",
+                       "launch": "one persistent launch per step from a CUDA graph"},
+            "roofline": {"bound": "hbm", "achieved": bytes_step / t_batch / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": bytes_step / t_batch / 1e9 / peak, "traffic": None,
+                         "peak_source": peak_src, "kernel": "k_batch"},
+            "plain_f64_per_factor": {"ms_per_step": t_plain * 1e3, "value": nnz / t_plain,
+                                     "speedup_of_batch": t_plain / t_batch},
+            "gpu_launches": args.steps, "clocks": clk,
+            "refine_sweeps_max": max(r["sweeps"] for r in reps)}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        worst = max(oracle.rel_error(x.cpu().numpy().reshape(A.n, -1), oracle.solve(A, b))
+                    for A, (_, b), x in zip(factors, rhs, xs))
+        line["err_vs_oracle"] = worst
+        t0 = time.perf_counter()
+        done = 0
+        for A, (_, b) in zip(factors, rhs):
+            oracle.solve(A, b)
+            done += A.nnz * nrhs
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"sequential FP64 solves of the first factors, 8 RHS each, {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    factors = [W.batch_factor(f) for f in range(256)]
+    rhs = [W.manufactured_rhs(A, 8, seed=7000 + i)[1] for i, A in enumerate(factors)]
+    t0 = time.perf_counter()
+    steps = 0
+    for _ in range(max(1, args.steps)):
+        for A, b in zip(factors, rhs):
+            oracle.solve(A, b)
+        steps += 1
+        if time.perf_counter() - t0 > 60:
+            break
+    el = time.perf_counter() - t0
+    nnz = sum(A.nnz for A in factors) * 8 * steps
+    v = nnz / el
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": steps, "warmup": 0, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "batch_256x8"},
+                      "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1,
+                                       "sample": f"{steps} passes over the 256 factors x 8 RHS"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+# ------------------------------------------------------------------ serving workload
+def _serve_setup(local, nfactors=64):
+    import torch
+
+    import paper_2503_05408_gb300 as sp
+    dev = f"cuda:{local}"
+    factors, plans, pools, xstars = [], [], [], []
+    g = torch.Generator(device=dev)
+    for f in range(nfactors):
+        A = W.serve_factor(f)
+        plans.append(sp.Plan(A, device=local))
+        g.manual_seed(9000 + f)
+        xs = (torch.rand((16, A.n), generator=g, device=dev, dtype=torch.float64) * 2 - 1).T   # col-major
+        L = torch.sparse_csr_tensor(torch.from_numpy(A.rowptr.astype(np.int64)),
+                                    torch.from_numpy(A.col.astype(np.int64)),
+                                    torch.from_numpy(A.val), size=(A.n, A.n)).to(dev)
+        b = (L @ xs.contiguous()).T.contiguous().T                                           # col-major (n, 16)
+        factors.append(A)
+        pools.append(b)
+        xstars.append(xs)
+    return factors, plans, pools, xstars
+
+
+def _replay(srv, fids, pools, xstars, arrival, fid, nrhs, deadline_s, check_every):
+    """Submit each request at its arrival time; poll completions; check a sample against x*."""
+    import torch
+    t0 = time.perf_counter()
+    outstanding = []
+    errs = []
+    submitted = 0
+    for i in range(len(arrival)):
+        while time.perf_counter() - t0 < arrival[i]:
+            pass
+        f, r = int(fid[i]), int(nrhs[i])
+        b = pools[f][:, :r]
+        x = torch.empty((r, b.shape[0]), dtype=torch.float64, device=b.device).T
+        rid = srv.submit(fids[f], b, x)
+        outstanding.append((rid, x, f, r, i % check_every == 0))
+        submitted += 1
+        keep = []
+        for k, item in enumerate(outstanding):
+            if k >= 64:                              # oldest first; later ones are polled next time
+                keep.append(item)
+                continue
+            rep = srv.poll(item[0])
+            if rep is None:
+                keep.append(item)
+            elif item[4]:
+                xv = item[1]
+                xr = xstars[item[2]][:, :item[3]]
+                errs.append(float((xv - xr).abs().max() / xr.abs().max()))
+        outstanding = keep
+        if time.perf_counter() - t0 > deadline_s:
+            break
+    # wait for the rest (bounded)
+    for item in outstanding:
+        remaining = deadline_s + 120 - (time.perf_counter() - t0)
+        if remaining <= 0:
+            break
+        try:
+            srv.wait(item[0], timeout=remaining)
+        except Exception:
+            continue
+        if item[4]:
+            xr = xstars[item[2]][:, :item[3]]
+            errs.append(float((item[1] - xr).abs().max() / xr.abs().max()))
+    return submitted, errs
+
+
+def run_serve(args):
+    """10,000 Poisson requests (2,000/s) against 64 resident factors (n log-uniform in
+    [10k, 2M], mixed kinds), 1-16 RHS each, FP32 sweeps + FP64 refinement, 40 GB budget;
+    compared with the plain FP64 per-request path (one launch per request, one stream)."""
+    import torch
+
+    import paper_2503_05408_gb300 as sp
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    t_setup = time.perf_counter()
+    factors, plans, pools, xstars = _serve_setup(local)
+    setup_s = time.perf_counter() - t_setup
+    arrival, fid, nrhs = W.serve_requests(args.serve_requests)
+    budget = 40 << 30
+    srv = sp.Server(budget, mode="continuous", precision=args.precision or "f32_refine", device=local,
+                    streams=32, max_batch=256)
+    fids = [srv.register(p) for p in plans]
+    # warm-up: one request per factor (module load, first launches)
+    for f in range(len(plans)):
+        b = pools[f][:, :1].contiguous()
+        x = torch.empty_like(b)
+        srv.wait(srv.submit(fids[f], b[:, 0], x[:, 0]), timeout=120)
+    srv.close()
+    srv = sp.Server(budget, mode="continuous", precision=args.precision or "f32_refine", device=local,
+                    streams=32, max_batch=256)
+    fids = [srv.register(p) for p in plans]
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    submitted, errs = _replay(srv, fids, pools, xstars, arrival, fid, nrhs, deadline_s=120.0, check_every=50)
+    srv.drain(timeout=300)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    # plain FP64 per-request baseline on the same stream, bounded in time
+    base = sp.Server(budget, mode="serial", precision="f64", device=local)
+    bf = [base.register(p) for p in plans]
+    nb = min(len(arrival), args.serve_baseline_requests)
+    bsub, berrs = _replay(base, bf, pools, xstars, arrival[:nb], fid[:nb], nrhs[:nb],
+                          deadline_s=args.baseline_seconds, check_every=10)
+    bst = base.stats()
+    base.close()
+    nnz_solved = float(sum(factors[int(f)].nnz * int(r) for f, r in zip(fid[:submitted], nrhs[:submitted])))
+    line = {"metric": "served solves/s (p50/p99 latency)", "value": st["solves_per_s"], "unit": "solves/s",
+            "n_gpus": world, "steps": submitted, "warmup": len(plans), "ms_per_step": 1e3 / max(st["solves_per_s"], 1e-9),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refine",
+            "data": "synthetic (seeded generators, Poisson arrivals)",
+            "config": {"workload": "serve_10k", "requests": submitted, "rate_per_s": 2000, "factors": len(plans),
+                       "sum_n": int(sum(A.n for A in factors)), "hbm_budget_gb": 40, "streams": 32,
+                       "setup_s": setup_s},
+            "served": {k: st[k] for k in ("completed", "p50_ms", "p99_ms", "max_ms", "mean_ms", "solves_per_s",
+                                          "launches", "mean_batch", "peak_workspace_bytes")},
+            "served_nnz_per_s": nnz_solved / wall,
+            "served_err_vs_manufactured_max": max(errs) if errs else None,
+            "plain_f64_per_request": {"submitted": bsub, **{k: bst[k] for k in ("completed", "p50_ms", "p99_ms",
+                                                                               "solves_per_s")},
+                                      "err_max": max(berrs) if berrs else None,
+                                      "note": f"first {nb} requests of the same stream (same arrival times); "
+                                              f"completed within {args.baseline_seconds + 120:.0f} s"},
+            "clocks": clk, "gpu_launches": st["launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle has no serving loop; "
+                      "the serving comparison is the plain FP64 per-request GPU path inside --workload serve_10k"}))
+    return 0
+
+
 SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta"}
 
 
 def main():
     args = parse_args()
+    if args.workload == "batch_256x8":
+        return run_batch_reference(args) if args.impl == "reference" else run_batch(args)
+    if args.workload == "serve_10k":
+        return run_serve_reference(args) if args.impl == "reference" else run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

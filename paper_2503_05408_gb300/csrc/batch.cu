@@ -37,7 +37,7 @@ namespace {
     } while (0)
 
 template <typename T>
-__device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *val, const T *diag) {
+__device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *val, const T *dinv) {
     SolveArgs<T> a;
     a.n = it.n;
     a.S = 0;
@@ -45,7 +45,7 @@ __device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *
     a.rp = it.rp;
     a.col = it.col;
     a.val = val;
-    a.diag = diag;
+    a.dinv = dinv;
     a.perm = it.perm;
     a.step_blk = nullptr;
     a.blk_phase = nullptr;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
         const BatchItem it = items[i];
         ItemResult out = {0, 1, 0.0, 0.0};
         if (!cfg.refine) {
-            SolveArgs<double> a = item_args<double>(it, it.val, it.diag);
+            SolveArgs<double> a = item_args<double>(it, it.val, it.dinv);
             a.b = static_cast<const double *>(it.b);
             a.x = static_cast<double *>(it.x);
             a.ldb = it.ldb;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
             walk_variant<double>(a, it, reinterpret_cast<double *>(smem_raw), dm, xm);
         } else {
             // FP32 sweeps with FP64 residual refinement, entirely inside this block
-            SolveArgs<float> a = item_args<float>(it, it.hi, it.dhi);
+            SolveArgs<float> a = item_args<float>(it, it.s32, it.dinv32);
             a.b = it.r32;
             a.ldb = it.n;
             a.x = it.d32;
@@ -273,7 +273,9 @@ void batch_fill_item(BatchItem &it, const sptrsv_plan *p, int nrhs, bool refine,
     it.perm = p->d.perm;
     it.phase_row = p->d.phase_row;
     it.val = p->d.val;
-    it.diag = p->d.diag;
+    it.dinv = p->d.dinv;
+    it.dinv32 = p->d.dinv32;
+    it.s32 = p->d.s32;
     it.hi = p->d.val_hi;
     it.lo = p->d.val_lo;
     it.dhi = p->d.diag_hi;
@@ -453,7 +455,9 @@ int sptrsv_batch_create(sptrsv_plan *const *plans, int32_t count, const int32_t 
             it.perm = p->d.perm;
             it.phase_row = p->d.phase_row;
             it.val = p->d.val;
-            it.diag = p->d.diag;
+            it.dinv = p->d.dinv;
+            it.dinv32 = p->d.dinv32;
+            it.s32 = p->d.s32;
             it.hi = p->d.val_hi;
             it.lo = p->d.val_lo;
             it.dhi = p->d.diag_hi;

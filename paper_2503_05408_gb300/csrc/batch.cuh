@@ -21,8 +21,9 @@ constexpr int kVariantLanes[V_COUNT] = {1, 2, 4, 4, 8, 16, 32};
 struct BatchItem {
     int32_t n, nphases, win, variant, nrhs;
     const int32_t *rp, *col, *perm, *phase_row;
-    const double *val, *diag;                       // FP64 values
-    const float *hi, *lo, *dhi, *dlo;               // FP32 split
+    const double *val, *dinv;                       // FP64 values, reciprocal diagonal
+    const float *hi, *lo, *dhi, *dlo;               // FP32 split (FP64 residual)
+    const float *s32, *dinv32;                      // FP32 sweep: scaled values, reciprocal diagonal
     double lnorm;
     const void *b;
     void *x;

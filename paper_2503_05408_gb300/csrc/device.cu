@@ -83,9 +83,14 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
     DeviceBuffers &d = p->d;
     if ((st = upload(rp, &d.rp, &bytes))) return st;
     if ((st = upload(col, &d.col, &bytes))) return st;
+    // rows scaled by their diagonal: x_i = b_i / A_ii - sum_j (A_ij / A_ii) x_j
+    std::vector<double> dinv(n), scaled(val.size());
+    for (int32_t i = 0; i < n; ++i) dinv[i] = 1.0 / diag[i];
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t q = rp[r]; q < rp[r + 1]; ++q) scaled[q] = val[q] * dinv[r];
     if (p->values & SPTRSV_VALUES_F64) {
-        if ((st = upload(val, &d.val, &bytes))) return st;
-        if ((st = upload(diag, &d.diag, &bytes))) return st;
+        if ((st = upload(scaled, &d.val, &bytes))) return st;
+        if ((st = upload(dinv, &d.dinv, &bytes))) return st;
     }
     if (p->values & SPTRSV_VALUES_F32) {
         // hi = fp32(v), lo = fp32(v - hi): hi + lo carries ~48 bits of v for the
@@ -101,8 +106,13 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
         }
         if ((st = upload(hi, &d.val_hi, &bytes))) return st;
         if ((st = upload(lo, &d.val_lo, &bytes))) return st;
+        std::vector<float> dinv32(n), s32(val.size());
+        for (int32_t i = 0; i < n; ++i) dinv32[i] = float(dinv[i]);
+        for (size_t q = 0; q < val.size(); ++q) s32[q] = float(scaled[q]);
         if ((st = upload(dhi, &d.diag_hi, &bytes))) return st;
         if ((st = upload(dlo, &d.diag_lo, &bytes))) return st;
+        if ((st = upload(dinv32, &d.dinv32, &bytes))) return st;
+        if ((st = upload(s32, &d.s32, &bytes))) return st;
     }
     if ((st = upload(h.dev_perm, &d.perm, &bytes))) return st;
     if ((st = upload(h.step_blk, &d.step_blk, &bytes))) return st;
@@ -122,9 +132,9 @@ void free_device(sptrsv_plan *p) {
     if (!p || p->device < 0) return;
     DeviceGuard g(p->device);
     DeviceBuffers &d = p->d;
-    void *ptrs[] = {d.rp,       d.col,      d.val,       d.diag,     d.val_hi, d.val_lo, d.diag_hi,
-                    d.diag_lo,  d.perm,     d.step_blk,  d.blk_phase, d.phase_row, d.counters,
-                    d.flags,    d.work};
+    void *ptrs[] = {d.rp,       d.col,      d.val,       d.dinv,      d.val_hi,    d.val_lo, d.diag_hi,
+                    d.diag_lo,  d.dinv32,   d.s32,       d.perm,      d.step_blk,  d.blk_phase, d.phase_row,
+                    d.counters, d.flags,    d.work};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     d = DeviceBuffers();
@@ -350,7 +360,7 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
 }
 
 template <typename T>
-SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *diag) {
+SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     SolveArgs<T> a;
     a.n = p->h.n;
     a.S = p->h.S;
@@ -358,7 +368,7 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *diag) {
     a.rp = p->d.rp;
     a.col = p->d.col;
     a.val = val;
-    a.diag = diag;
+    a.dinv = dinv;
     a.perm = p->d.perm;
     a.step_blk = p->d.step_blk;
     a.blk_phase = p->d.blk_phase;
@@ -407,11 +417,11 @@ int check_solve_args(const sptrsv_plan *p, const void *b, const void *x, int32_t
 }
 
 template <typename T>
-int plain_solve(sptrsv_plan *p, const T *val, const T *diag, const void *b, void *x, int32_t nrhs, int64_t ld,
+int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void *x, int32_t nrhs, int64_t ld,
                 const sptrsv_solve_opts &o, cudaStream_t s, LaunchCfg &c) {
     int st = choose<T>(p, o, nrhs, c);
     if (st) return st;
-    SolveArgs<T> a = base_args<T>(p, val, diag);
+    SolveArgs<T> a = base_args<T>(p, val, dinv);
     a.nrhs = nrhs;
     a.b = static_cast<const T *>(b);
     a.x = static_cast<T *>(x);
@@ -463,7 +473,7 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     ra.ctl = reinterpret_cast<Ctl *>(p->d.counters);
     ra.dtol = o.refine_tol;
     const int rgrid = std::max(1, std::min(4 * p->num_sms, (n + 255) / 256));
-    SolveArgs<float> a = base_args<float>(p, p->d.val_hi, p->d.diag_hi);
+    SolveArgs<float> a = base_args<float>(p, p->d.s32, p->d.dinv32);
     a.nrhs = nrhs;
     a.b = r32;
     a.ldb = n;
@@ -494,12 +504,12 @@ int solve_impl(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld,
     if (dtype == SPTRSV_F64) {
         if (o.precision == SPTRSV_PREC_F64) {
             if (!(p->values & SPTRSV_VALUES_F64)) return fail(SPTRSV_ERR_ARG, "plan has no FP64 values");
-            return plain_solve<double>(p, p->d.val, p->d.diag, b, x, nrhs, ld, o, s, c);
+            return plain_solve<double>(p, p->d.val, p->d.dinv, b, x, nrhs, ld, o, s, c);
         }
         return refine_solve(p, static_cast<const double *>(b), static_cast<double *>(x), nrhs, ld, o, s, c);
     }
     if (!(p->values & SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "plan has no FP32 values");
-    return plain_solve<float>(p, p->d.val_hi, p->d.diag_hi, b, x, nrhs, ld, o, s, c);
+    return plain_solve<float>(p, p->d.s32, p->d.dinv32, b, x, nrhs, ld, o, s, c);
 }
 
 int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_report *report, bool refine,

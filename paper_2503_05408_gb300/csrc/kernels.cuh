@@ -54,8 +54,8 @@ struct SolveArgs {
     int32_t n, S, nrhs;
     const int32_t *__restrict__ rp;
     const int32_t *__restrict__ col;
-    const T *__restrict__ val;
-    const T *__restrict__ diag;
+    const T *__restrict__ val;       // off-diagonal values scaled by 1 / diagonal
+    const T *__restrict__ dinv;      // reciprocal of the diagonal (scales b)
     const int32_t *__restrict__ perm;
     const int32_t *__restrict__ step_blk;
     const int32_t *__restrict__ blk_phase;
@@ -201,6 +201,16 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
     return v;
 }
 
+// Sum over the first `width` lanes of the group only (lanes >= width hold zeros):
+// ceil(log2(width)) shuffle steps instead of log2(LANES) on the critical path.
+template <typename T, int LANES>
+__device__ __forceinline__ T group_sum_width(T v, unsigned mask, int width) {
+#pragma unroll
+    for (int off = LANES / 2; off > 0; off >>= 1)
+        if (off < width) v += __shfl_xor_sync(mask, v, off, LANES);
+    return v;
+}
+
 // Eq. 2.1 for device row r: x[perm[r]] = (b[perm[r]] - sum_q val[q] x[col[q]]) / diag[r],
 // LANES lanes cooperating on the row, looping over the right-hand sides.
 template <typename T, int LANES>
@@ -208,14 +218,14 @@ __device__ __forceinline__ void row_solve(const SolveArgs<T> &a, int r, int lane
                                           double &xm) {
     const int beg = a.rp[r], end = a.rp[r + 1];
     const int orow = a.perm[r];
-    const T dg = a.diag[r];
+    const T dv = a.dinv[r];
     for (int j = 0; j < a.nrhs; ++j) {
         const T *xj = a.x + (int64_t)j * a.ldx;
         T acc = T(0);
         for (int q = beg + lane; q < end; q += LANES) acc += a.val[q] * xj[a.col[q]];
         acc = group_sum<T, LANES>(acc, mask);
         if (lane == 0) {
-            const T y = (a.b[orow + (int64_t)j * a.ldb] - acc) / dg;
+            const T y = a.b[orow + (int64_t)j * a.ldb] * dv - acc;
             a.x[orow + (int64_t)j * a.ldx] = y;
             if (a.refine) refine_apply(a, orow, j, y, dm, xm);
         }
@@ -238,6 +248,11 @@ __device__ __forceinline__ void rows_span(const SolveArgs<T> &a, int r0, int r1,
 
 // ----------------------------------------------------------------------------
 // Row registers and the value-polling protocol.
+//
+// Rows are pre-scaled by the analysis: the device keeps v'_ij = A_ij / A_ii and
+// 1 / A_ii, so Eq. 2.1 becomes x_i = b_i / A_ii - sum_j v'_ij x_j: one FMA per
+// parent and no division or trailing multiply on the dependency chain (FP64
+// arithmetic has long latency on this part, so the chain is kept short).
 //
 // A row's structure (row pointers, original id, diagonal, right-hand side,
 // columns and values) does not depend on x, so every executor loads it ahead
@@ -283,7 +298,7 @@ __device__ __forceinline__ void st_pub(float *p, float v) {
 template <typename T, int U>
 struct RowRegs {
     int beg, end, orow;
-    T dg;
+    T dinv;
     T b0;          // right-hand side of column 0 (lane 0), prefetched with the entries
     int c[U];
     T v[U];
@@ -294,7 +309,7 @@ __device__ __forceinline__ void load_meta(const SolveArgs<T> &a, int r, RowRegs<
     m.beg = __ldg(a.rp + r);
     m.end = __ldg(a.rp + r + 1);
     m.orow = __ldg(a.perm + r);
-    m.dg = __ldg(a.diag + r);
+    m.dinv = __ldg(a.dinv + r);
 }
 
 // RP (right-hand-side parallel tile): every lane of the group holds the same U
@@ -319,7 +334,7 @@ __device__ __forceinline__ void load_entries(const SolveArgs<T> &a, int lane, Ro
 
 // Spin until *p is no longer SENTINEL; bounded by the status word and the timeout.
 template <typename T>
-__device__ __noinline__ bool poll_wait(const T *p, T &v, const SolveArgs<T> &a, unsigned long long &waits) {
+__device__ __forceinline__ bool poll_wait(const T *p, T &v, const SolveArgs<T> &a, unsigned long long &waits) {
     ++waits;
     const long long t0 = gtimer();
     unsigned spins = 0;
@@ -364,9 +379,9 @@ __device__ __forceinline__ bool row_exec_rp(const SolveArgs<T> &a, const RowRegs
             for (int u = 0; u < U; ++u)
                 if (ok && m.c[u] >= 0 && is_sentinel(xv[u])) ok = poll_wait(xj + m.c[u], xv[u], a, waits);
         }
-        T acc = T(0);
+        T acc = bj * m.dinv;
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc += m.v[u] * xv[u];
+        for (int u = 0; u < U; ++u) acc -= m.v[u] * xv[u];
         for (int q = m.beg + U; ok && q < m.end; ++q) {
             const int c = __ldg(a.col + q);
             T xc;
@@ -375,10 +390,10 @@ __device__ __forceinline__ bool row_exec_rp(const SolveArgs<T> &a, const RowRegs
                 xc = ld_poll(xj + c);
                 if (is_sentinel(xc)) ok = poll_wait(xj + c, xc, a, waits);
             } else xc = xj[c];
-            acc += __ldg(a.val + q) * xc;
+            acc -= __ldg(a.val + q) * xc;
         }
         if (!ok) break;
-        const T y = (bj - acc) / m.dg;
+        const T y = acc;
         T *dst = a.x + m.orow + (int64_t)j * a.ldx;
         if constexpr (MODE == 1) st_pub(dst, publishable(y));
         else *dst = y;
@@ -409,14 +424,49 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
                 xv[u] = T(0);
             }
         }
+        // lane 0 carries the scaled right-hand side, every lane subtracts its parents
+        T acc = (lane == 0) ? bj * m.dinv : T(0);
         if constexpr (MODE == 1) {
+            // accumulate each parent as soon as its value lands: after the last
+            // arrival only one FMA remains on the dependency chain (the order, and so
+            // the last-bit rounding, follows arrival order)
+            unsigned pend = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (ok && m.c[u] >= 0 && is_sentinel(xv[u])) ok = poll_wait(xj + m.c[u], xv[u], a, waits);
+            for (int u = 0; u < U; ++u) {
+                if (m.c[u] >= 0) {
+                    if (is_sentinel(xv[u])) pend |= 1u << u;
+                    else acc -= m.v[u] * xv[u];
+                }
+            }
+            if (pend) {
+                ++waits;
+                long long t0 = 0;
+                unsigned spins = 0;
+                while (pend) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (pend & (1u << u)) xv[u] = ld_poll(xj + m.c[u]);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if ((pend & (1u << u)) && !is_sentinel(xv[u])) {
+                            acc -= m.v[u] * xv[u];
+                            pend &= ~(1u << u);
+                        }
+                    if (pend && (++spins & 63u) == 1) {
+                        if (spins == 1) t0 = gtimer();
+                        else if (ld_status(a.ctl) != 0) { ok = false; break; }
+                        else if (gtimer() - t0 > a.timeout_ns) {
+                            raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc -= m.v[u] * xv[u];
         }
-        T acc = T(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc += m.v[u] * xv[u];
         // entries beyond the register tile (long rows)
         for (int q = m.beg + lane + U * LANES; ok && q < m.end; q += LANES) {
             const int c = __ldg(a.col + q);
@@ -426,14 +476,14 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
                 xc = ld_poll(xj + c);
                 if (is_sentinel(xc)) ok = poll_wait(xj + c, xc, a, waits);
             } else xc = xj[c];
-            acc += __ldg(a.val + q) * xc;
+            acc -= __ldg(a.val + q) * xc;
         }
         if constexpr (MODE == 1) {
             if (!__all_sync(mask, ok)) return false;
         }
-        acc = group_sum<T, LANES>(acc, mask);
+        acc = group_sum_width<T, LANES>(acc, mask, m.end - m.beg + 1);
         if (lane == 0) {
-            const T y = (bj - acc) / m.dg;
+            const T y = acc;
             T *dst = a.x + m.orow + (int64_t)j * a.ldx;
             if constexpr (MODE == 1) st_pub(dst, publishable(y));
             else *dst = y;

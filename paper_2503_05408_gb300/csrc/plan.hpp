@@ -46,10 +46,12 @@ struct DeviceBuffers {
     // matrix in device-row order; column ids stay ORIGINAL row ids
     int32_t *rp = nullptr;        // n + 1, off-diagonal entries only
     int32_t *col = nullptr;       // nnz_off
-    double *val = nullptr;        // nnz_off (VALUES_F64)
-    double *diag = nullptr;       // n
+    double *val = nullptr;        // nnz_off (VALUES_F64): A_ij / A_ii
+    double *dinv = nullptr;       // n: 1 / diagonal, rounded once on the host
     float *val_hi = nullptr, *val_lo = nullptr;    // nnz_off (VALUES_F32)
-    float *diag_hi = nullptr, *diag_lo = nullptr;  // n
+    float *diag_hi = nullptr, *diag_lo = nullptr;  // n: FP32 split of the diagonal (residual)
+    float *dinv32 = nullptr;      // n: fp32(1 / diagonal) for the FP32 sweeps
+    float *s32 = nullptr;         // nnz_off: fp32(A_ij / A_ii), the FP32 sweeps' scaled values
     int32_t *perm = nullptr;      // n: device row -> original row
     int32_t *step_blk = nullptr, *blk_phase = nullptr, *phase_row = nullptr;
     // scratch

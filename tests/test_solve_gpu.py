@@ -141,7 +141,8 @@ def test_diagonal_only_is_one_superstep():
     plan = sp.Plan(A)
     for sync in ("grid", "flags", "cta"):
         x, rep = solve_gpu(plan, b, sync=sync)
-        assert np.array_equal(x[:, 0], b[:, 0] / A.val)      # one IEEE division per row
+        # x = b * (1/d): the reciprocal is rounded once on the host, so at most two roundings
+        assert np.max(np.abs(x[:, 0] - b[:, 0] / A.val) / np.abs(b[:, 0] / A.val)) <= 4.5e-16
     assert rep["barriers"] == 0
 
 
