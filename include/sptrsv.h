@@ -148,7 +148,10 @@ enum {
     SPTRSV_SYNC_AUTO = 0,   /* autotuned per plan                                          */
     SPTRSV_SYNC_GRID = 1,   /* persistent grid, one grid-wide barrier per superstep         */
     SPTRSV_SYNC_FLAGS = 2,  /* persistent grid, per-row ready flags on cross-CTA parents    */
-    SPTRSV_SYNC_CTA = 3     /* one thread block walks all supersteps (small factors)        */
+    SPTRSV_SYNC_CTA = 3,    /* one thread block walks all supersteps (small factors); each
+                               phase is staged into shared memory by TMA bulk copies ahead of
+                               use when the plan's largest phase fits                       */
+    SPTRSV_SYNC_CTA_REGS = 4 /* one thread block, register prefetch only (no staging)       */
 };
 enum {
     SPTRSV_PREC_F64 = 0,         /* FP64 values and arithmetic (needs SPTRSV_VALUES_F64)    */

@@ -25,11 +25,12 @@ ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE = -10, -11, -12
 SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
-SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA = 0, 1, 2, 3
+SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS = 0, 1, 2, 3, 4
 PREC_F64, PREC_F32_REFINE = 0, 1
 
-SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta"}
-_SYNC = {"auto": SYNC_AUTO, "grid": SYNC_GRID, "flags": SYNC_FLAGS, "cta": SYNC_CTA}
+SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta",
+              SYNC_CTA_REGS: "cta_regs"}
+_SYNC = {v: k for k, v in SYNC_NAMES.items()}
 _MODE = {"levels": SCHED_LEVELS, "growlocal": SCHED_GROWLOCAL}
 _PREC = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}
 

@@ -73,15 +73,40 @@ __device__ __noinline__ void walk_call(const SolveArgs<T> &a, int nphases, int w
     walk_block<T, L, U, RING, RP>(a, nphases, win, xs, dm, xm);
 }
 
+template <typename T, int L, bool RING, bool RP>
+__device__ __noinline__ bool staged_call(const SolveArgs<T> &a, const StageInfo &si, int nphases, int win,
+                                         unsigned char *smem, double &dm, double &xm) {
+    return walk_block_staged<T, L, RING, RP>(a, si, nphases, win, smem, dm, xm);
+}
+
+// Returns false if a bounded wait of the staged walk failed.
 template <typename T>
-__device__ __forceinline__ void walk_variant(const SolveArgs<T> &a, const BatchItem &it, T *xs, double &dm,
-                                             double &xm) {
+__device__ __forceinline__ bool walk_variant(const SolveArgs<T> &a, const BatchItem &it, unsigned char *smem,
+                                             double &dm, double &xm) {
     const bool ring = it.win > 0;
+    if (it.staged) {
+        StageInfo si = it.si;
+        si.bdev = it.bdev;
+#define SPTRSV_STAGED(L, RP)                                                                   \
+    return ring ? staged_call<T, L, true, RP>(a, si, it.nphases, it.win, smem, dm, xm)         \
+                : staged_call<T, L, false, RP>(a, si, it.nphases, 0, smem, dm, xm);
+        switch (it.variant) {
+            case V_L1: SPTRSV_STAGED(1, false)
+            case V_L2: SPTRSV_STAGED(2, false)
+            case V_L4: SPTRSV_STAGED(4, false)
+            case V_T4: SPTRSV_STAGED(4, true)
+            case V_T8: SPTRSV_STAGED(8, true)
+            case V_T16: SPTRSV_STAGED(16, true)
+            default: SPTRSV_STAGED(32, true)
+        }
+#undef SPTRSV_STAGED
+    }
+    T *xs = reinterpret_cast<T *>(smem);
 #define SPTRSV_WALK(L, U, RP)                                                              \
     {                                                                                      \
         if (ring) walk_call<T, L, U, true, RP>(a, it.nphases, it.win, xs, dm, xm);         \
         else walk_call<T, L, U, false, RP>(a, it.nphases, 0, xs, dm, xm);                 \
-        return;                                                                            \
+        return true;                                                                       \
     }
     switch (it.variant) {
         case V_L1: SPTRSV_WALK(1, 4, false)
@@ -147,7 +172,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
             a.ldb = it.ldb;
             a.ldx = it.ldx;
             double dm = 0.0, xm = 0.0;
-            walk_variant<double>(a, it, reinterpret_cast<double *>(smem_raw), dm, xm);
+            if (!walk_variant<double>(a, it, smem_raw, dm, xm)) out.status = SPTRSV_ERR_TIMEOUT;
         } else {
             // FP32 sweeps with FP64 residual refinement, entirely inside this block
             SolveArgs<float> a = item_args<float>(it, it.s32, it.dinv32);
@@ -166,7 +191,10 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
             for (int t = 0;; ++t) {
                 a.refine = t == 0 ? 1 : 2;
                 double dm = 0.0, xm = 0.0;
-                walk_variant<float>(a, it, reinterpret_cast<float *>(smem_raw), dm, xm);
+                if (!walk_variant<float>(a, it, smem_raw, dm, xm)) {
+                    out.status = SPTRSV_ERR_TIMEOUT;
+                    break;
+                }
                 ++sweeps;
                 __syncthreads();
                 dmax = block_max(dm, s_scratch);
@@ -183,7 +211,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchItem *__restrict__ 
             out.sweeps = sweeps;
             out.dnorm = xmax > 0.0 ? dmax / xmax : 0.0;
             out.berr = berr;
-            out.status = conv ? 0 : SPTRSV_ERR_NOT_CONVERGED;
+            if (!out.status) out.status = conv ? 0 : SPTRSV_ERR_NOT_CONVERGED;
         }
         if (threadIdx.x == 0) res[i] = out;
         __syncthreads();
@@ -257,9 +285,35 @@ int item_win(const sptrsv_plan *p, int nrhs, size_t elem, size_t budget) {
 }
 
 constexpr size_t kBatchRingBudget = 64 * 1024;     // per block: leaves room for 2-3 blocks per SM
+constexpr size_t kBatchStageBudget = 96 * 1024;    // staged walk per block: 2 blocks per SM
 }  // namespace
 
 int batch_default_variant(const sptrsv_plan *p, int nrhs) { return default_variant_impl(p, nrhs); }
+
+size_t batch_item_workspace(const BatchItem &it, bool refine) {
+    const size_t es = refine ? sizeof(float) : sizeof(double);
+    const size_t v = (size_t(it.n) * size_t(it.nrhs) * sizeof(float) + 255) & ~size_t(255);
+    size_t w = refine ? 2 * v : 0;
+    if (it.staged) w += (size_t(it.n) * size_t(it.nrhs) * es + 64 + 255) & ~size_t(255);
+    return w;
+}
+
+void batch_bind_workspace(BatchItem &it, char *base, bool refine) {
+    const size_t v = (size_t(it.n) * size_t(it.nrhs) * sizeof(float) + 255) & ~size_t(255);
+    size_t off = 0;
+    if (refine) {
+        it.r32 = reinterpret_cast<float *>(base);
+        it.d32 = reinterpret_cast<float *>(base + v);
+        off = 2 * v;
+    }
+    it.bdev = it.staged ? static_cast<void *>(base + off) : nullptr;
+}
+
+size_t batch_item_smem(const BatchItem &it, bool refine) {
+    const size_t es = refine ? sizeof(float) : sizeof(double);
+    const size_t ring = size_t(it.win) * size_t(it.nrhs) * es;
+    return it.staged ? stage_smem_bytes(it.si, ring) : ring;
+}
 
 void batch_fill_item(BatchItem &it, const sptrsv_plan *p, int nrhs, bool refine, size_t ring_budget) {
     it = BatchItem{};
@@ -281,6 +335,11 @@ void batch_fill_item(BatchItem &it, const sptrsv_plan *p, int nrhs, bool refine,
     it.dhi = p->d.diag_hi;
     it.dlo = p->d.diag_lo;
     it.lnorm = p->lnorm;
+    // staged walk when the factor's largest phase fits the block's shared-memory budget
+    const size_t es = refine ? sizeof(float) : sizeof(double);
+    stage_slot_layout(size_t(p->h.max_phase_rows), size_t(p->h.max_phase_ents), nrhs, es, it.si);
+    it.si.phase_ent = p->d.phase_ent;
+    it.staged = stage_smem_bytes(it.si, size_t(it.win) * size_t(nrhs) * es) <= kBatchStageBudget ? 1 : 0;
 }
 
 namespace {
@@ -439,32 +498,14 @@ int sptrsv_batch_create(sptrsv_plan *const *plans, int32_t count, const int32_t 
     B->threads = threads;
     B->plans.assign(plans, plans + count);
     B->nrhs.assign(nrhs, nrhs + count);
-    const size_t elem = refine ? sizeof(float) : sizeof(double);
     size_t work = 0;
     for (int32_t f = 0; f < count; ++f) {
         const sptrsv_plan *p = plans[f];
         for (int32_t c0 = 0; c0 < nrhs[f]; c0 += 32) {       // items of at most 32 columns
-            BatchItem it{};
-            it.n = p->h.n;
-            it.nphases = int32_t(p->h.phase_row.size()) - 1;
-            it.nrhs = std::min(32, nrhs[f] - c0);
-            it.win = item_win(p, it.nrhs, elem, kBatchRingBudget);
-            it.variant = default_variant_impl(p, it.nrhs);
-            it.rp = p->d.rp;
-            it.col = p->d.col;
-            it.perm = p->d.perm;
-            it.phase_row = p->d.phase_row;
-            it.val = p->d.val;
-            it.dinv = p->d.dinv;
-            it.dinv32 = p->d.dinv32;
-            it.s32 = p->d.s32;
-            it.hi = p->d.val_hi;
-            it.lo = p->d.val_lo;
-            it.dhi = p->d.diag_hi;
-            it.dlo = p->d.diag_lo;
-            it.lnorm = p->lnorm;
-            B->smem = std::max(B->smem, size_t(it.win) * size_t(it.nrhs) * elem);
-            if (refine) work += 2 * ((size_t(it.n) * it.nrhs * sizeof(float) + 255) & ~size_t(255));
+            BatchItem it;
+            batch_fill_item(it, p, std::min(32, nrhs[f] - c0), refine, kBatchRingBudget);
+            B->smem = std::max(B->smem, batch_item_smem(it, refine));
+            work += batch_item_workspace(it, refine);
             B->items.push_back(it);
             B->item_factor.push_back(f);
             B->item_col0.push_back(c0);
@@ -499,13 +540,11 @@ int sptrsv_batch_create(sptrsv_plan *const *plans, int32_t count, const int32_t 
         (void)cudaGetLastError();
         st = fail(e == cudaErrorMemoryAllocation ? SPTRSV_ERR_OOM : SPTRSV_ERR_CUDA, cudaGetErrorString(e));
     }
-    if (!st && refine) {
+    if (!st && work) {
         char *w = static_cast<char *>(B->d_work);
         for (BatchItem &it : B->items) {
-            const size_t v = (size_t(it.n) * it.nrhs * sizeof(float) + 255) & ~size_t(255);
-            it.r32 = reinterpret_cast<float *>(w);
-            it.d32 = reinterpret_cast<float *>(w + v);
-            w += 2 * v;
+            batch_bind_workspace(it, w, refine);
+            w += batch_item_workspace(it, refine);
         }
     }
     if (prev >= 0 && prev != device) cudaSetDevice(prev);

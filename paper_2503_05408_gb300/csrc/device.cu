@@ -35,10 +35,13 @@ int device_sm_count(int device, int32_t *out) {
 
 namespace {
 
+// Every device array carries 64 zeroed bytes past its end: the staged walker's
+// 16-byte aligned bulk copies may round a slice up by up to 12 bytes.
 template <typename T>
 int upload(const std::vector<T> &h, T **d, int64_t *bytes) {
-    const size_t nb = std::max<size_t>(h.size(), 1) * sizeof(T);
+    const size_t nb = h.size() * sizeof(T) + 64;
     CUDA_TRY(cudaMalloc((void **)d, nb));
+    CUDA_TRY(cudaMemset(*d, 0, nb));
     if (!h.empty()) CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     *bytes += int64_t(nb);
     return SPTRSV_OK;
@@ -118,6 +121,14 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
     if ((st = upload(h.step_blk, &d.step_blk, &bytes))) return st;
     if ((st = upload(h.blk_phase, &d.blk_phase, &bytes))) return st;
     if ((st = upload(h.phase_row, &d.phase_row, &bytes))) return st;
+    {
+        std::vector<int32_t> pent(h.phase_row.size());
+        int32_t mx = 0;
+        for (size_t q = 0; q < pent.size(); ++q) pent[q] = rp[h.phase_row[q]];
+        for (size_t q = 0; q + 1 < pent.size(); ++q) mx = std::max(mx, pent[q + 1] - pent[q]);
+        p->h.max_phase_ents = mx;
+        if ((st = upload(pent, &d.phase_ent, &bytes))) return st;
+    }
     CUDA_TRY(cudaMalloc((void **)&d.counters, sizeof(Ctl)));
     CUDA_TRY(cudaMemset(d.counters, 0, sizeof(Ctl)));
     bytes += sizeof(Ctl);
@@ -134,6 +145,7 @@ void free_device(sptrsv_plan *p) {
     DeviceBuffers &d = p->d;
     void *ptrs[] = {d.rp,       d.col,      d.val,       d.dinv,      d.val_hi,    d.val_lo, d.diag_hi,
                     d.diag_lo,  d.dinv32,   d.s32,       d.perm,      d.step_blk,  d.blk_phase, d.phase_row,
+                    d.phase_ent,
                     d.counters, d.flags,    d.work};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -210,9 +222,46 @@ WalkKern<T> walk_kernel(int lanes) {
     }
 }
 
+template <typename T>
+using StageKern = void (*)(SolveArgs<T>, StageInfo, int, int);
+
+template <typename T, bool RING, bool RP>
+StageKern<T> stage_kernel(int lanes) {
+    if constexpr (RP) {
+        switch (lanes) {
+            case 4: return k_stage<T, 4, RING, true>;
+            case 8: return k_stage<T, 8, RING, true>;
+            case 16: return k_stage<T, 16, RING, true>;
+            case 32: return k_stage<T, 32, RING, true>;
+            default: return nullptr;
+        }
+    } else {
+        switch (lanes) {
+            case 1: return k_stage<T, 1, RING, false>;
+            case 2: return k_stage<T, 2, RING, false>;
+            case 4: return k_stage<T, 4, RING, false>;
+            case 8: return k_stage<T, 8, RING, false>;
+            case 32: return k_stage<T, 32, RING, false>;
+            default: return nullptr;
+        }
+    }
+}
+
+// Shared-memory slot layout of the staged walker for this plan and RHS count;
+// returns the slot size in bytes.
+template <typename T>
+size_t stage_layout(const sptrsv_plan *p, int nrhs, StageInfo &si) {
+    const size_t b = stage_slot_layout(size_t(p->h.max_phase_rows), size_t(p->h.max_phase_ents), nrhs, sizeof(T), si);
+    si.phase_ent = p->d.phase_ent;
+    return b;
+}
+constexpr size_t kStageSmemMax = 200 * 1024;
+
 struct LaunchCfg {
     int sync, lanes, threads, grid;
-    int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA)
+    int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
+                       // 4 staged walk (one CTA, TMA-staged phases)
+    StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
     bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
     size_t smem;
@@ -240,6 +289,9 @@ int tune_slot(int32_t dtype, int32_t precision, int32_t nrhs) {
 
 template <typename T, bool RP>
 const void *kernel_ptr_rp(const LaunchCfg &c) {
+    if (c.kind == 4)
+        return c.win ? reinterpret_cast<const void *>(stage_kernel<T, true, RP>(c.lanes))
+                     : reinterpret_cast<const void *>(stage_kernel<T, false, RP>(c.lanes));
     switch (c.kind) {
         case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes));
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
@@ -299,12 +351,22 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         c.kind = wide_phases(p) ? 1 : 2;
         if (c.kind == 2 && c.rp) c.rp = false, c.lanes = auto_lanes(p);   // block executor: entry lanes
     }
-    else if (c.sync == SPTRSV_SYNC_CTA) {
+    else if (c.sync == SPTRSV_SYNC_CTA || c.sync == SPTRSV_SYNC_CTA_REGS) {
         c.kind = 3;
         const int w = p->h.ring_rows;
-        if (w > 0 && size_t(w) * size_t(nrhs) * sizeof(T) <= kRingBytesMax) {
+        const size_t ring = size_t(w) * size_t(nrhs) * sizeof(T);
+        if (w > 0 && ring <= kRingBytesMax) {
             c.win = w;
-            c.smem = size_t(w) * size_t(nrhs) * sizeof(T);
+            c.smem = ring;
+        }
+        if (c.sync == SPTRSV_SYNC_CTA) {
+            const size_t slot = stage_layout<T>(p, nrhs, c.si);
+            (void)slot;
+            const size_t need = stage_smem_bytes(c.si, c.win ? ring : 0);
+            if (need <= kStageSmemMax && c.threads >= 64) {   // one warp of the block only produces
+                c.kind = 4;
+                c.smem = need;
+            }
         }
     } else {
         return fail(SPTRSV_ERR_ARG, "unknown sync mode");
@@ -314,7 +376,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c.smem));
         if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     }
-    if (c.kind == 3) {
+    if (c.kind >= 3) {
         c.grid = 1;
         return SPTRSV_OK;
     }
@@ -339,7 +401,7 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = (c.kind == 3) ? 0 : 1;   // co-residency guaranteed or error
+    attr[0].val.cooperative = (c.kind >= 3) ? 0 : 1;   // co-residency guaranteed or error
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
@@ -347,6 +409,8 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     const void *k = kernel_ptr<T>(c);
     if (c.kind == 0 || c.kind == 2) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<Kern<T>>(const_cast<void *>(k)), args);
+    } else if (c.kind == 4) {
+        e = cudaLaunchKernelEx(&cfg, reinterpret_cast<StageKern<T>>(const_cast<void *>(k)), args, c.si, nph, c.win);
     } else {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<WalkKern<T>>(const_cast<void *>(k)), args, nph,
                                c.kind == 3 ? c.win : 0);
@@ -427,6 +491,10 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
     a.x = static_cast<T *>(x);
     a.ldb = a.ldx = ld;
     a.timeout_ns = (long long)(o.timeout_s * 1e9);
+    if (c.kind == 4) {      // staged walk: b in device order, row-major, in the plan workspace
+        if ((st = ensure_work(p, size_t(p->h.n) * size_t(nrhs) * sizeof(T) + 256))) return st;
+        c.si.bdev = p->d.work;
+    }
     if (c.kind == 0) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
         CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
     }
@@ -451,9 +519,11 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     if (st) return st;
     const int32_t n = p->h.n;
     const size_t vec = size_t(n) * size_t(nrhs) * sizeof(float);
-    if ((st = ensure_work(p, 2 * vec + 256))) return st;
+    const size_t vpad = (vec + 255) & ~size_t(255);
+    if ((st = ensure_work(p, 3 * vpad + 256))) return st;
     float *r32 = static_cast<float *>(p->d.work);
-    float *d32 = reinterpret_cast<float *>(static_cast<char *>(p->d.work) + ((vec + 255) & ~size_t(255)));
+    float *d32 = reinterpret_cast<float *>(static_cast<char *>(p->d.work) + vpad);
+    c.si.bdev = static_cast<char *>(p->d.work) + 2 * vpad;       // staged walk: b in device order
     CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
     ResidualArgs ra;
     ra.n = n;
@@ -608,15 +678,16 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     if (nrhs >= 2)
         for (int tile : {4, 8, 16, 32})
             if (tile / 2 < nrhs) maps.push_back({tile, 0});
-    for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
-        if (sync == SPTRSV_SYNC_CTA && !small) continue;
+    for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_CTA_REGS, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
+        if ((sync == SPTRSV_SYNC_CTA || sync == SPTRSV_SYNC_CTA_REGS) && !small) continue;
         for (auto [tile, lanes] : maps) {
             for (int t : {128, 256, 512})
                 for (int bps : {1, 2}) {
-                    if (sync == SPTRSV_SYNC_CTA && bps > 1) continue;
+                    const bool one_block = sync == SPTRSV_SYNC_CTA || sync == SPTRSV_SYNC_CTA_REGS;
+                    if (one_block && bps > 1) continue;
                     sptrsv_solve_opts c = o;
                     c.sync = sync; c.rhs_tile = tile; c.lanes = lanes; c.threads = t;
-                    c.blocks_per_sm = sync == SPTRSV_SYNC_CTA ? 0 : bps;
+                    c.blocks_per_sm = one_block ? 0 : bps;
                     cands.push_back(c);
                 }
         }

@@ -23,6 +23,7 @@
 // SPTRSV_ERR_TIMEOUT in the status word and returns - it never traps.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 
@@ -579,6 +580,296 @@ __device__ __forceinline__ void walk_block(const SolveArgs<T> &a, int nphases, i
         pb2 = pb3;
         pb3 = pb4;
     }
+}
+
+// ----------------------------------------------------------------------------
+// Staged single-block walker.  Each phase's rows are contiguous in device order,
+// and so are their row pointers, original ids, reciprocal diagonals, columns,
+// values and - after the block has copied b into device order once - their
+// right-hand sides.  One elected thread copies those six slices with TMA bulk
+// copies (cp.async.bulk, completion counted on an mbarrier) three phases ahead
+// into a four-slot shared-memory ring; the phase boundaries it needs arrive
+// through a small cp.async FIFO.  A phase then costs one mbarrier wait, the
+// rows' arithmetic out of shared memory and one block barrier: no dependent
+// global load remains on the chain except the gathers of x when no
+// shared-memory x ring is available.  Every wait is bounded; a failed wait
+// ends the walk for the whole block.
+// ----------------------------------------------------------------------------
+struct StageInfo {
+    const int32_t *phase_ent;        // entry offset of every phase boundary (rp[phase_row[q]])
+    void *bdev;                      // workspace: b in device order, row-major (n x nrhs), 16-byte aligned
+    int32_t rows_cap, ents_cap;      // largest phase of the plan
+    int32_t slot_bytes;              // bytes of one ring slot (16-byte multiple)
+    int32_t off_perm, off_dinv, off_col, off_val, off_b;   // slot layout
+};
+
+// Host: slot layout for phases of at most `rows` rows / `ents` entries and nrhs
+// right-hand sides of `elem` bytes; returns the slot size.
+inline size_t stage_slot_layout(size_t rows, size_t ents, int nrhs, size_t elem, StageInfo &si) {
+    auto a16 = [](size_t v) { return (v + 15) & ~size_t(15); };
+    size_t off = a16((rows + 8) * 4);                       // row pointers
+    si.off_perm = int32_t(off);
+    off += a16((rows + 8) * 4);
+    si.off_dinv = int32_t(off);
+    off += a16((rows + 8) * elem);
+    si.off_col = int32_t(off);
+    off += a16((ents + 8) * 4);
+    si.off_val = int32_t(off);
+    off += a16((ents + 8) * elem);
+    si.off_b = int32_t(off);
+    off += a16((rows * size_t(nrhs) + 8) * elem);
+    si.slot_bytes = int32_t(off);
+    si.rows_cap = int32_t(rows);
+    si.ents_cap = int32_t(ents);
+    si.bdev = nullptr;
+    return off;
+}
+// Dynamic shared memory of a staged walk: 4 mbarriers, 4 slots, optional x ring.
+inline size_t stage_smem_bytes(const StageInfo &si, size_t ring_bytes) { return 64 + 4 * size_t(si.slot_bytes) + ring_bytes; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_4() { asm volatile("cp.async.wait_group 4;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// 16-byte aligned superset [lo, hi) of element range [a, b) for elements of `esz` bytes.
+__device__ __forceinline__ int align_lo(int a, int esz) { return a & ~(16 / esz - 1); }
+__device__ __forceinline__ int align_hi(int b, int esz) { return (b + 16 / esz - 1) & ~(16 / esz - 1); }
+
+template <typename T>
+struct StageSlot {
+    int32_t *rp, *perm, *col;
+    T *dinv, *val, *b;
+    int srp, sperm, sdinv, scol, sval, sb;  // first element of each copied slice
+};
+
+template <typename T>
+__device__ __forceinline__ StageSlot<T> stage_slot(unsigned char *base, const StageInfo &si, int p0, int e0,
+                                                   int nrhs) {
+    StageSlot<T> s;
+    s.rp = reinterpret_cast<int32_t *>(base);
+    s.perm = reinterpret_cast<int32_t *>(base + si.off_perm);
+    s.dinv = reinterpret_cast<T *>(base + si.off_dinv);
+    s.col = reinterpret_cast<int32_t *>(base + si.off_col);
+    s.val = reinterpret_cast<T *>(base + si.off_val);
+    s.b = reinterpret_cast<T *>(base + si.off_b);
+    s.srp = align_lo(p0, 4);
+    s.sperm = align_lo(p0, 4);
+    s.sdinv = align_lo(p0, sizeof(T));
+    s.scol = align_lo(e0, 4);
+    s.sval = align_lo(e0, sizeof(T));
+    s.sb = align_lo(p0 * nrhs, sizeof(T));
+    return s;
+}
+
+// Producer side: bulk-copy phase [p0, p1) with entries [e0, e1) into the slot.
+template <typename T>
+__device__ __forceinline__ void stage_issue(const SolveArgs<T> &a, unsigned char *base, const StageInfo &si,
+                                            uint64_t *bar, int p0, int p1, int e0, int e1) {
+    const StageSlot<T> s = stage_slot<T>(base, si, p0, e0, a.nrhs);
+    const uint32_t nrp = uint32_t(align_hi(p1 + 1, 4) - s.srp) * 4u;
+    const uint32_t nperm = uint32_t(align_hi(p1, 4) - s.sperm) * 4u;
+    const uint32_t ndinv = uint32_t(align_hi(p1, sizeof(T)) - s.sdinv) * uint32_t(sizeof(T));
+    const uint32_t ncol = e1 > e0 ? uint32_t(align_hi(e1, 4) - s.scol) * 4u : 0u;
+    const uint32_t nval = e1 > e0 ? uint32_t(align_hi(e1, sizeof(T)) - s.sval) * uint32_t(sizeof(T)) : 0u;
+    const uint32_t nb = uint32_t(align_hi(p1 * a.nrhs, sizeof(T)) - s.sb) * uint32_t(sizeof(T));
+    // the slot's previous readers finished before the block barrier that precedes this issue
+    mbar_expect_tx(bar, nrp + nperm + ndinv + ncol + nval + nb);
+    bulk_g2s(s.rp, a.rp + s.srp, nrp, bar);
+    bulk_g2s(s.perm, a.perm + s.sperm, nperm, bar);
+    bulk_g2s(s.dinv, a.dinv + s.sdinv, ndinv, bar);
+    if (ncol) bulk_g2s(s.col, a.col + s.scol, ncol, bar);
+    if (nval) bulk_g2s(s.val, a.val + s.sval, nval, bar);
+    bulk_g2s(s.b, static_cast<const T *>(si.bdev) + s.sb, nb, bar);
+}
+
+// Bounded wait on a slot's mbarrier; returns false on timeout (status recorded when ctl is set).
+template <typename T>
+__device__ __forceinline__ bool stage_wait(const SolveArgs<T> &a, uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer() - t0 > (a.timeout_ns > 0 ? a.timeout_ns : 2000000000LL)) {
+            if (a.ctl) raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Rows of one staged phase (MODE 0: x from global, MODE 2: x from the shared ring).
+template <typename T, int LANES, int MODE, bool RP>
+__device__ __forceinline__ void stage_rows(const SolveArgs<T> &a, const StageSlot<T> &s, int p0, int p1, int g, int G,
+                                           int lane, unsigned mask, T *xs, int win, double &dm, double &xm) {
+    const int R = a.nrhs;
+    for (int lr = g; lr < p1 - p0; lr += G) {
+        const int r = p0 + lr;
+        const int beg = s.rp[r - s.srp], end = s.rp[r + 1 - s.srp];
+        const int orow = s.perm[r - s.sperm];
+        const T dv = s.dinv[r - s.sdinv];
+        const T *bb = s.b + (r * R - s.sb);
+        if constexpr (RP) {
+            for (int j = lane; j < R; j += LANES) {
+                const T *xj = a.x + (int64_t)j * a.ldx;
+                T acc = bb[j] * dv;
+                for (int q = beg; q < end; ++q) {
+                    const int c = s.col[q - s.scol];
+                    const T xc = MODE == 2 ? xs[(c & (win - 1)) + j * win] : xj[c];
+                    acc -= s.val[q - s.sval] * xc;
+                }
+                a.x[orow + (int64_t)j * a.ldx] = acc;
+                if constexpr (MODE == 2) xs[(orow & (win - 1)) + j * win] = acc;
+                if (a.refine) refine_apply(a, orow, j, acc, dm, xm);
+            }
+        } else {
+            for (int j = 0; j < R; ++j) {
+                const T *xj = a.x + (int64_t)j * a.ldx;
+                T acc = (lane == 0) ? bb[j] * dv : T(0);
+                for (int q = beg + lane; q < end; q += LANES) {
+                    const int c = s.col[q - s.scol];
+                    const T xc = MODE == 2 ? xs[(c & (win - 1)) + j * win] : xj[c];
+                    acc -= s.val[q - s.sval] * xc;
+                }
+                acc = group_sum_width<T, LANES>(acc, mask, end - beg + 1);
+                if (lane == 0) {
+                    a.x[orow + (int64_t)j * a.ldx] = acc;
+                    if constexpr (MODE == 2) xs[(orow & (win - 1)) + j * win] = acc;
+                    if (a.refine) refine_apply(a, orow, j, acc, dm, xm);
+                }
+            }
+        }
+    }
+}
+
+// smem: [4 mbarriers (64 B)] [4 slots of si.slot_bytes] [x ring of win * nrhs * sizeof(T)]
+template <typename T, int LANES, bool RING, bool RP>
+__device__ __forceinline__ bool walk_block_staged(const SolveArgs<T> &a, const StageInfo &si, int nphases, int win,
+                                                  unsigned char *smem, double &dm, double &xm) {
+    constexpr int RPW = 32 / LANES;
+    constexpr int MODE = RING ? 2 : 0;
+    constexpr int NS = 4, NQ = 8;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *slots = smem + 64;
+    T *xs = reinterpret_cast<T *>(slots + NS * si.slot_bytes);
+    __shared__ int s_b[NS][4];          // p0, p1, e0, e1 of the phase held by each slot
+    __shared__ __align__(16) int s_q[NQ][2];   // producer FIFO: phase_row, phase_ent of future boundaries
+    const int lane32 = threadIdx.x & 31;
+    const int grp = lane32 / LANES, lane = lane32 % LANES;
+    const unsigned mask = group_mask<LANES>(lane32);
+    // the last warp only produces (bulk copies, boundary FIFO) so that its issue
+    // work overlaps the other warps' rows instead of delaying a computing warp
+    const int nwarps = blockDim.x >> 5;
+    const bool producer = (threadIdx.x >> 5) == nwarps - 1;
+    const int pthread = (nwarps - 1) * 32;
+    const int g = (threadIdx.x >> 5) * RPW + grp;
+    const int G = (nwarps - 1) * RPW;
+    const int R = a.nrhs;
+    // b in device order, row-major, written by this block for the bulk copies (async proxy)
+    T *bdev = static_cast<T *>(si.bdev);
+    const int n_rows = a.phase_row[nphases];
+    for (int i = threadIdx.x; i < n_rows * R; i += blockDim.x) {
+        const int r = i / R, j = i - r * R;
+        bdev[i] = a.b[__ldg(a.perm + r) + (int64_t)j * a.ldb];
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (threadIdx.x == pthread) {
+        for (int i = 0; i < NS; ++i) mbar_init(bars + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == pthread) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        for (int q = 0; q < 3 && q < nphases; ++q) {
+            const int p0 = a.phase_row[q], p1 = a.phase_row[q + 1];
+            const int e0 = si.phase_ent[q], e1 = si.phase_ent[q + 1];
+            s_b[q][0] = p0; s_b[q][1] = p1; s_b[q][2] = e0; s_b[q][3] = e1;
+            stage_issue<T>(a, slots + q * si.slot_bytes, si, bars + q, p0, p1, e0, e1);
+        }
+        // FIFO: boundary i (i = 3 .. 3 + NQ - 1) in entry i % NQ, one cp.async group each
+        for (int i = 3; i < 3 + NQ; ++i) {
+            if (i <= nphases) {
+                cp_async<4>(&s_q[i % NQ][0], a.phase_row + i);
+                cp_async<4>(&s_q[i % NQ][1], si.phase_ent + i);
+            }
+            cp_async_commit();
+        }
+    }
+    __syncthreads();
+    // one block barrier per phase: it also carries the readiness of the next slot
+    bool ok = nphases == 0 || stage_wait(a, bars, 0);
+    bool stop = __syncthreads_or(!ok);
+    for (int q = 0; q < nphases && !stop; ++q) {
+        const int slot = q & (NS - 1);
+        if (producer) {
+            // phase q+3 (boundaries q+3, q+4 from the FIFO) into the slot phase q-1
+            // released at the last barrier; overlaps the other warps' rows
+            if (threadIdx.x == pthread && q + 3 < nphases) {
+                cp_async_wait_4();          // boundaries up to q + 4 have landed
+                const int sl = (q + 3) & (NS - 1);
+                const int p0 = s_q[(q + 3) % NQ][0], e0 = s_q[(q + 3) % NQ][1];
+                const int p1 = s_q[(q + 4) % NQ][0], e1 = s_q[(q + 4) % NQ][1];
+                s_b[sl][0] = p0; s_b[sl][1] = p1; s_b[sl][2] = e0; s_b[sl][3] = e1;
+                stage_issue<T>(a, slots + sl * si.slot_bytes, si, bars + sl, p0, p1, e0, e1);
+                const int i = q + 3 + NQ;  // refill the FIFO entry of boundary q + 3
+                if (i <= nphases) {
+                    cp_async<4>(&s_q[i % NQ][0], a.phase_row + i);
+                    cp_async<4>(&s_q[i % NQ][1], si.phase_ent + i);
+                }
+                cp_async_commit();
+            }
+        } else {
+            const int p0 = s_b[slot][0], p1 = s_b[slot][1];
+            const StageSlot<T> s = stage_slot<T>(slots + slot * si.slot_bytes, si, p0, s_b[slot][2], R);
+            stage_rows<T, LANES, MODE, RP>(a, s, p0, p1, g, G, lane, mask, xs, win, dm, xm);
+        }
+        if (q + 1 < nphases) ok = stage_wait(a, bars + ((q + 1) & (NS - 1)), ((q + 1) / NS) & 1);
+        stop = __syncthreads_or(!ok);
+    }
+    if (threadIdx.x == pthread) {
+        cp_async_wait_0();
+        if (ok)                            // every barrier phase has completed: retire them
+            for (int i = 0; i < NS; ++i)
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bars + i)) : "memory");
+    }
+    __syncthreads();
+    return ok;
+}
+
+template <typename T, int LANES, bool RING, bool RP>
+__global__ void __launch_bounds__(512, 1) k_stage(SolveArgs<T> a, StageInfo si, int nphases, int win) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (refine_skip(a)) return;
+    double dm = 0.0, xm = 0.0;
+    walk_block_staged<T, LANES, RING, RP>(a, si, nphases, win, smem_raw, dm, xm);
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
 }
 
 // Maximum over the thread block (every thread gets the result).

@@ -37,6 +37,7 @@ struct HostSchedule {
     std::vector<int32_t> step_blk, blk_phase, phase_row;
     int32_t max_phase_rows = 0;
     int32_t max_block_rows = 0;
+    int32_t max_phase_ents = 0;   // largest number of off-diagonal entries in one phase
     // Smallest power-of-two ring (rows) that can hold x in shared memory when one
     // thread block walks the phases in order (0 = none up to kMaxRingRows).
     int32_t ring_rows = 0;
@@ -54,6 +55,7 @@ struct DeviceBuffers {
     float *s32 = nullptr;         // nnz_off: fp32(A_ij / A_ii), the FP32 sweeps' scaled values
     int32_t *perm = nullptr;      // n: device row -> original row
     int32_t *step_blk = nullptr, *blk_phase = nullptr, *phase_row = nullptr;
+    int32_t *phase_ent = nullptr; // entry offset (device-order row pointer) of every phase boundary
     // scratch
     unsigned long long *counters = nullptr;  // [0] barrier, [1] barriers done, [2] flag waits,
                                              // [3] work cursor, [4..] refinement norms

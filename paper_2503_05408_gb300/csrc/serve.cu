@@ -109,11 +109,14 @@ struct Arena {
 };
 
 constexpr size_t kServeRingBudget = 64 * 1024;
+constexpr size_t kServeSmem = 96 * 1024;          // dynamic shared memory of every serving launch
 
+// Upper bound of a request's workspace (refinement vectors + staged right-hand sides).
 size_t workspace_bytes(const sptrsv_plan *p, int nrhs, bool refine) {
-    if (!refine) return 0;
     const size_t v = (size_t(p->h.n) * size_t(nrhs) * sizeof(float) + 255) & ~size_t(255);
-    return 2 * v;
+    const size_t bdev = (size_t(p->h.n) * size_t(nrhs) * (refine ? sizeof(float) : sizeof(double)) + 64 + 255) &
+                        ~size_t(255);
+    return (refine ? 2 * v : 0) + bdev;
 }
 
 }  // namespace
@@ -200,23 +203,20 @@ bool continuous_step(sptrsv_server *S) {
                 const uint64_t id = S->pending.front();
                 Request &r = S->reqs[id];
                 const sptrsv_plan *p = S->factors[r.fid];
+                BatchItem &it = sl.h_items[cnt];
+                batch_fill_item(it, p, r.nrhs, S->refine, kServeRingBudget);
+                if (batch_item_smem(it, S->refine) > S->smem) it.staged = 0;   // launch smem is fixed
                 size_t off = 0;
-                const size_t need = workspace_bytes(p, r.nrhs, S->refine);
+                const size_t need = batch_item_workspace(it, S->refine);
                 if (!S->arena.alloc(need, off)) break;             // FIFO: wait for memory
                 S->pending.pop_front();
                 r.state = 1;
                 r.ws_off = off;
                 r.ws_bytes = need;
-                BatchItem &it = sl.h_items[cnt];
-                batch_fill_item(it, p, r.nrhs, S->refine, kServeRingBudget);
                 it.b = r.b;
                 it.x = r.x;
                 it.ldb = it.ldx = r.ld;
-                if (S->refine) {
-                    const size_t v = need / 2;
-                    it.r32 = reinterpret_cast<float *>(S->arena.base + off);
-                    it.d32 = reinterpret_cast<float *>(S->arena.base + off + v);
-                }
+                if (need) batch_bind_workspace(it, S->arena.base + off, S->refine);
                 sl.reqs.push_back(id);
                 ++cnt;
             }
@@ -284,7 +284,7 @@ void worker_main(sptrsv_server *S) {
 }
 
 int ensure_arena(sptrsv_server *S) {
-    if (S->arena_mem || !S->refine) return SPTRSV_OK;
+    if (S->arena_mem) return SPTRSV_OK;
     if (S->factor_bytes >= S->budget) return fail(SPTRSV_ERR_BUDGET, "resident factors fill the HBM budget");
     size_t size = S->budget - S->factor_bytes;
     cudaError_t e = cudaMalloc(&S->arena_mem, size);
@@ -342,7 +342,7 @@ int sptrsv_serve_create(size_t hbm_budget, const sptrsv_serve_opts *opts, sptrsv
     cudaSetDevice(S->device);
     int st = SPTRSV_OK;
     cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
-    S->smem = kServeRingBudget;
+    S->smem = kServeSmem;
     st = batch_occupancy(S->threads, S->smem, &S->per_sm);
     const int nslots = o.mode == SPTRSV_SERVE_SERIAL_F64 ? 1 : o.streams;
     S->slots.resize(nslots);
@@ -395,7 +395,7 @@ int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, do
     if (factor_id < 0 || factor_id >= int32_t(S->factors.size())) return fail(SPTRSV_ERR_ARG, "unknown factor id");
     const sptrsv_plan *p = S->factors[factor_id];
     if (ld < std::max<int64_t>(p->h.n, 1)) return fail(SPTRSV_ERR_ARG, "ld < n");
-    if (!S->arena_mem && S->refine) {
+    if (!S->arena_mem && S->opts.mode == SPTRSV_SERVE_CONTINUOUS) {
         int prev = -1;
         cudaGetDevice(&prev);
         cudaSetDevice(S->device);
@@ -403,7 +403,7 @@ int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, do
         if (prev >= 0) cudaSetDevice(prev);
         if (st) return st;
     }
-    const size_t need = workspace_bytes(p, nrhs, S->refine);
+    const size_t need = S->opts.mode == SPTRSV_SERVE_CONTINUOUS ? workspace_bytes(p, nrhs, S->refine) : 0;
     if (need > S->arena.size) {
         ++S->rejected;
         return fail(SPTRSV_ERR_BUDGET, "request workspace exceeds the HBM budget left by the resident factors");

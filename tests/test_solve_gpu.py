@@ -59,7 +59,7 @@ SMALL = {
 
 
 @pytest.mark.parametrize("name", sorted(SMALL))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("lanes", [1, 4, 32])
 def test_f64_levels_parity(name, sync, lanes):
     A = SMALL[name]()
@@ -74,7 +74,7 @@ def test_f64_levels_parity(name, sync, lanes):
 
 
 @pytest.mark.parametrize("name", ["lap2d_64x64", "er_30k", "nb_20k", "banded_20k"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("k", [1, 8, 152])
 def test_f64_growlocal_parity(name, sync, k):
     A = SMALL[name]()
@@ -89,7 +89,7 @@ def test_f64_growlocal_parity(name, sync, k):
     assert oracle.rel_error(x, xo) <= F64_TOL
 
 
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0), (37, 3)])
 @pytest.mark.parametrize("rhs_tile", [0, 1, 4, 32])
 def test_multi_rhs(sync, nrhs, ld_pad, rhs_tile):
@@ -129,7 +129,7 @@ def test_edge_sizes(n):
     A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
     b = np.ones((n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta"):
+    for sync in ("grid", "flags", "cta", "cta_regs"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert np.allclose(x[:, 0], 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)
 
@@ -186,7 +186,7 @@ REFINE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(REFINE_CASES))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_refine_parity(name, sync, nrhs):
     A = REFINE_CASES[name]()
@@ -244,3 +244,16 @@ def test_full_size_random_refine():
     for sync in ("flags", "grid"):
         x, rep = solve_gpu(plan, b, sync=sync, precision="f32_refine")
         assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+def test_staged_walker_matches_register_walker():
+    # same per-row arithmetic in the same order; only FMA contraction of the first
+    # term may differ, so the two one-block walkers agree to rounding
+    for A in (W.laplace2d_lower(4096, 64), W.random_window_lower(20_000, 4, 64, 8),
+              W.make_dominant(W.narrow_band_lower(20_000, 0.05, 20, 9))):
+        xs, b = W.manufactured_rhs(A, 3, seed=17)
+        plan = sp.Plan(A)
+        for tile in (1, 4):
+            x1, r1 = solve_gpu(plan, b, sync="cta", rhs_tile=tile)
+            x2, r2 = solve_gpu(plan, b, sync="cta_regs", rhs_tile=tile)
+            assert np.max(np.abs(x1 - x2)) <= 1e-14 * np.max(np.abs(x2))
