@@ -496,11 +496,106 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
 }
 
 // ----------------------------------------------------------------------------
+// Polled row, entry-split lanes, driven by a warp-uniform loop.  Every group of
+// the warp publishes its row in the poll round in which its last parent
+// arrives, independently of the other groups: a warp holding 32/LANES rows
+// never makes a finished row wait for a slower sibling.  `has_row` is false for
+// groups past the end of the factor; they only take part in the votes.
+// ----------------------------------------------------------------------------
+template <typename T, int LANES, int U>
+__device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const RowRegs<T, U> &m, bool has_row,
+                                                int lane, unsigned gmask, unsigned long long &waits,
+                                                double &dm, double &xm) {
+    constexpr unsigned kAll = 0xffffffffu;
+    // the widest row of the warp sets the (warp-uniform) shuffle depth
+    int width = has_row ? m.end - m.beg + 1 : 1;
+    if constexpr (LANES > 1) width = __reduce_max_sync(kAll, width);
+    for (int j = 0; j < a.nrhs; ++j) {
+        const T *xj = a.x + (int64_t)j * a.ldx;
+        T acc = T(0);
+        unsigned pend = 0;
+        int q = has_row ? m.beg + lane + U * LANES : 0;     // next entry beyond the register tile
+        bool tail = has_row && q < m.end;
+        if (has_row) {
+            if (lane == 0) acc = (j == 0 ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb]) * m.dinv;
+            T xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = m.c[u] >= 0 ? ld_poll(xj + m.c[u]) : T(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (m.c[u] >= 0) {
+                    if (is_sentinel(xv[u])) pend |= 1u << u;
+                    else acc -= m.v[u] * xv[u];
+                }
+            }
+            if (pend) ++waits;
+        }
+        bool published = !has_row;
+        unsigned spins = 0;
+        long long t0 = 0;
+        // No lane ever blocks inside an iteration: a parent may be a row of this
+        // same warp, published only at the vote below.
+        while (true) {
+            const unsigned busy = __ballot_sync(kAll, pend != 0 || tail);
+            const bool fin = !published && (busy & gmask) == 0;
+            if (__any_sync(kAll, fin)) {
+                T y = acc;
+                if constexpr (LANES > 1) y = group_sum_width<T, LANES>(y, kAll, width);
+                if (fin && lane == 0) {
+                    st_pub(a.x + m.orow + (int64_t)j * a.ldx, publishable(y));
+                    if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+                }
+                published = published || fin;
+            }
+            if (busy == 0) break;
+            if (pend) {
+                // one more round of loads for this lane's missing parents; each is
+                // subtracted as soon as it lands
+                T xv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (pend & (1u << u)) xv[u] = ld_poll(xj + m.c[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if ((pend & (1u << u)) && !is_sentinel(xv[u])) {
+                        acc -= m.v[u] * xv[u];
+                        pend &= ~(1u << u);
+                    }
+            } else if (tail) {
+                // entries beyond the register tile (long rows), in order, while ready
+                while (q < m.end) {
+                    const int c = __ldg(a.col + q);
+                    const T xc = ld_poll(xj + c);
+                    if (is_sentinel(xc)) break;
+                    acc -= __ldg(a.val + q) * xc;
+                    q += LANES;
+                }
+                tail = q < m.end;
+            }
+            if ((++spins & 63u) == 1) {                      // warp-uniform bound on the wait
+                if (spins == 1) {
+                    t0 = gtimer();
+                } else {
+                    const bool expired = gtimer() - t0 > a.timeout_ns;
+                    if (__any_sync(kAll, ld_status(a.ctl) != 0 || expired)) {
+                        if (expired && lane == 0) raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
+                        return false;
+                    }
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// ----------------------------------------------------------------------------
 // Polled executor (SPTRSV_SYNC_FLAGS).  Rows are dealt to groups round-robin
 // in device order and each group handles its rows in increasing order: the
 // smallest unfinished row always has finished parents and an owner at it, so
 // with every block co-resident the walk cannot deadlock.  Two-stage software
-// pipeline: metadata two rows ahead, columns/values one row ahead.
+// pipeline: metadata two rows ahead, columns/values one row ahead.  Entry-split
+// warps advance together (warp-uniform loop, per-group publication); right-hand-
+// side tiles run one row per group.
 // ----------------------------------------------------------------------------
 template <typename T, int LANES, int U, bool RP>
 __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
@@ -508,24 +603,35 @@ __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
     const int lane32 = threadIdx.x & 31;
     const int grp = lane32 / LANES, lane = lane32 % LANES;
     const unsigned mask = group_mask<LANES>(lane32);
-    const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + grp;
+    const int wbase = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW;     // the warp's first row
     const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
     if (refine_skip(a)) return;
     unsigned long long waits = 0;
     double dm = 0.0, xm = 0.0;
     RowRegs<T, U> cur, nxt, nn;
-    int r = g;
+    int r = wbase + grp;
     if (r < a.n) {
         load_meta(a, r, cur);
         load_entries<T, LANES, U, RP>(a, lane, cur);
     }
     if (r + G < a.n) load_meta(a, r + G, nxt);
-    for (; r < a.n; r += G) {
-        if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
-        if (r + G < a.n) load_entries<T, LANES, U, RP>(a, lane, nxt);
-        if (!row_exec<T, LANES, U, 1, RP>(a, cur, lane, mask, nullptr, 0, waits, dm, xm)) break;
-        cur = nxt;
-        nxt = nn;
+    if constexpr (RP) {
+        for (; r < a.n; r += G) {
+            if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
+            if (r + G < a.n) load_entries<T, LANES, U, RP>(a, lane, nxt);
+            if (!row_exec<T, LANES, U, 1, RP>(a, cur, lane, mask, nullptr, 0, waits, dm, xm)) break;
+            cur = nxt;
+            nxt = nn;
+        }
+    } else {
+        for (int rb = wbase; rb < a.n; rb += G) {                                // warp-uniform
+            r = rb + grp;
+            if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
+            if (r + G < a.n) load_entries<T, LANES, U, RP>(a, lane, nxt);
+            if (!row_exec_polled<T, LANES, U>(a, cur, r < a.n, lane, mask, waits, dm, xm)) break;
+            cur = nxt;
+            nxt = nn;
+        }
     }
     if (waits) atomicAdd(&a.ctl->flag_waits, waits);
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
