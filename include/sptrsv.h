@@ -151,7 +151,17 @@ enum {
     SPTRSV_SYNC_CTA = 3,    /* one thread block walks all supersteps (small factors); each
                                phase is staged into shared memory by TMA bulk copies ahead of
                                use when the plan's largest phase fits                       */
-    SPTRSV_SYNC_CTA_REGS = 4 /* one thread block, register prefetch only (no staging)       */
+    SPTRSV_SYNC_CTA_REGS = 4, /* one thread block, register prefetch only (no staging)      */
+    SPTRSV_SYNC_LOCAL = 5   /* persistent grid, one block per SM (threads up to 1024); rows
+                               partitioned over the blocks so that most dependencies, above
+                               all each row's last-finishing parent, stay inside one block
+                               (Sec. 3's locality principle applied to SMs); a block keeps its
+                               rows' values in shared memory and polls them there, other
+                               parents in global memory.  One right-hand side per solve
+                               (nrhs == 1).  The partition is built on the first solve in this
+                               mode (synchronous: device-to-host copy, host pass, upload) and
+                               kept in the plan.  ARG if nrhs > 1 or if the rows do not fit the
+                               shared memory of the grid's blocks                            */
 };
 enum {
     SPTRSV_PREC_F64 = 0,         /* FP64 values and arithmetic (needs SPTRSV_VALUES_F64)    */
@@ -173,7 +183,14 @@ typedef struct {
                             nrhs >= 3), 1 = lanes split each row's entries, 4/8/16/32 = a tile of
                             that many right-hand sides per row, each row's columns and values
                             loaded once for the whole tile                                     */
+    int32_t eager_sum;   /* SYNC_FLAGS / SYNC_LOCAL with 2..8 lanes splitting a row's entries: SPTRSV_EAGER_*.
+                            ON: while a row waits for its last parents its lanes keep the
+                            partial sum reduced, so the lane that receives the last parent
+                            publishes after one FMA (best when a row's parents finish at
+                            different times); OFF: reduce once all parents are in (best when
+                            they arrive together, e.g. stencils).  AUTO = tuned value, else ON */
 } sptrsv_solve_opts;
+enum { SPTRSV_EAGER_AUTO = 0, SPTRSV_EAGER_ON = 1, SPTRSV_EAGER_OFF = 2 };
 
 void sptrsv_solve_opts_default(sptrsv_solve_opts *o);
 

@@ -25,11 +25,11 @@ ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE = -10, -11, -12
 SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
-SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS = 0, 1, 2, 3, 4
+SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL = 0, 1, 2, 3, 4, 5
 PREC_F64, PREC_F32_REFINE = 0, 1
 
 SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta",
-              SYNC_CTA_REGS: "cta_regs"}
+              SYNC_CTA_REGS: "cta_regs", SYNC_LOCAL: "local"}
 _SYNC = {v: k for k, v in SYNC_NAMES.items()}
 _MODE = {"levels": SCHED_LEVELS, "growlocal": SCHED_GROWLOCAL}
 _PREC = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}
@@ -64,7 +64,8 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("sync", ctypes.c_int32), ("lanes", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("max_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("timeout_s", ctypes.c_double), ("rhs_tile", ctypes.c_int32)]
+                ("timeout_s", ctypes.c_double), ("rhs_tile", ctypes.c_int32),
+                ("eager_sum", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -256,7 +257,7 @@ class Plan:
                                      ctypes.byref(solve_opts(**base)), _stream_handle(stream),
                                      ctypes.byref(best), ctypes.byref(ms)))
         out = {"sync": best.sync, "lanes": best.lanes, "threads": best.threads,
-               "blocks_per_sm": best.blocks_per_sm, "rhs_tile": best.rhs_tile}
+               "blocks_per_sm": best.blocks_per_sm, "rhs_tile": best.rhs_tile, "eager_sum": best.eager_sum}
         self.tuned_ms = ms.value
         return out
 

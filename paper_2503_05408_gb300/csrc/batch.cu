@@ -50,6 +50,7 @@ __device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *
     a.step_blk = nullptr;
     a.blk_phase = nullptr;
     a.phase_row = it.phase_row;
+    a.blk_row = nullptr;
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;

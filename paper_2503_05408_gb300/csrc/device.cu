@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -146,7 +147,9 @@ void free_device(sptrsv_plan *p) {
     void *ptrs[] = {d.rp,       d.col,      d.val,       d.dinv,      d.val_hi,    d.val_lo, d.diag_hi,
                     d.diag_lo,  d.dinv32,   d.s32,       d.perm,      d.step_blk,  d.blk_phase, d.phase_row,
                     d.phase_ent,
-                    d.counters, d.flags,    d.work};
+                    d.counters, d.flags,    d.work,
+                    d.l_rp,     d.l_col,    d.l_perm,    d.l_blk_row, d.l_val,     d.l_dinv, d.l_s32,
+                    d.l_dinv32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     d = DeviceBuffers();
@@ -169,7 +172,7 @@ bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lane
 bool rp_ok(int tile) { return tile == 4 || tile == 8 || tile == 16 || tile == 32; }
 
 template <typename T, bool RP>
-Kern<T> flags_kernel(int lanes) {
+Kern<T> flags_kernel(int lanes, bool pre) {
     if constexpr (RP) {
         switch (lanes) {
             case 4: return k_flags<T, 4, kRpTile, true>;
@@ -181,12 +184,23 @@ Kern<T> flags_kernel(int lanes) {
     } else {
         switch (lanes) {
             case 1: return k_flags<T, 1, tile_for(1), false>;
-            case 2: return k_flags<T, 2, tile_for(2), false>;
-            case 4: return k_flags<T, 4, tile_for(4), false>;
-            case 8: return k_flags<T, 8, tile_for(8), false>;
-            case 32: return k_flags<T, 32, tile_for(32), false>;
+            case 2: return pre ? k_flags<T, 2, tile_for(2), false, true> : k_flags<T, 2, tile_for(2), false>;
+            case 4: return pre ? k_flags<T, 4, tile_for(4), false, true> : k_flags<T, 4, tile_for(4), false>;
+            case 8: return pre ? k_flags<T, 8, tile_for(8), false, true> : k_flags<T, 8, tile_for(8), false>;
+            case 32: return pre ? k_flags<T, 32, tile_for(32), false, true> : k_flags<T, 32, tile_for(32), false>;
             default: return nullptr;
         }
+    }
+}
+template <typename T>
+Kern<T> local_kernel(int lanes, bool pre) {
+    switch (lanes) {
+        case 1: return k_local<T, 1, tile_for(1), false>;
+        case 2: return pre ? k_local<T, 2, tile_for(2), true> : k_local<T, 2, tile_for(2), false>;
+        case 4: return pre ? k_local<T, 4, tile_for(4), true> : k_local<T, 4, tile_for(4), false>;
+        case 8: return pre ? k_local<T, 8, tile_for(8), true> : k_local<T, 8, tile_for(8), false>;
+        case 32: return pre ? k_local<T, 32, tile_for(32), true> : k_local<T, 32, tile_for(32), false>;
+        default: return nullptr;
     }
 }
 template <typename T>
@@ -260,10 +274,11 @@ constexpr size_t kStageSmemMax = 200 * 1024;
 struct LaunchCfg {
     int sync, lanes, threads, grid;
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
-                       // 4 staged walk (one CTA, TMA-staged phases)
+                       // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled)
     StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
     bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
+    bool eager;        // polled executor: eager group sum (SPTRSV_EAGER_ON)
     size_t smem;
 };
 
@@ -293,7 +308,8 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
         return c.win ? reinterpret_cast<const void *>(stage_kernel<T, true, RP>(c.lanes))
                      : reinterpret_cast<const void *>(stage_kernel<T, false, RP>(c.lanes));
     switch (c.kind) {
-        case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes));
+        case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager));
+        case 5: return RP ? nullptr : reinterpret_cast<const void *>(local_kernel<T>(c.lanes, c.eager));
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
         case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
         default:
@@ -304,6 +320,166 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
 template <typename T>
 const void *kernel_ptr(const LaunchCfg &c) {
     return c.rp ? kernel_ptr_rp<T, true>(c) : kernel_ptr_rp<T, false>(c);
+}
+
+// ------------------------------------------------------------------ block-local layout
+// Rows are assigned to nb thread blocks in (wavefront, id) order.  A row goes to
+// the block holding most of its parents of the two previous wavefronts (weight
+// 4 for the previous wavefront, which holds its last-finishing parent, 1 for
+// the one before), as long as that block has taken fewer than
+// ceil(1.25 * width / nb) rows of the row's wavefront; otherwise to the block
+// with the fewest rows of this wavefront (then the fewest rows overall).  The
+// cap keeps every wavefront spread over all blocks, the vote keeps dependency
+// chains inside a block.
+constexpr double kLocalSlack = 1.25;
+
+void free_local(DeviceBuffers &d) {
+    void *ptrs[] = {d.l_rp, d.l_col, d.l_perm, d.l_blk_row, d.l_val, d.l_dinv, d.l_s32, d.l_dinv32};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    d.l_rp = d.l_col = d.l_perm = d.l_blk_row = nullptr;
+    d.l_val = d.l_dinv = nullptr;
+    d.l_s32 = d.l_dinv32 = nullptr;
+    d.loc_nb = 0;
+    d.loc_smem = 0;
+    d.loc_bytes = 0;
+}
+
+template <typename T>
+int download(const T *dptr, size_t count, std::vector<T> &h) {
+    h.resize(count);
+    if (count) CUDA_TRY(cudaMemcpy(h.data(), dptr, count * sizeof(T), cudaMemcpyDeviceToHost));
+    return SPTRSV_OK;
+}
+
+int ensure_local(sptrsv_plan *p, int nb) {
+    DeviceBuffers &d = p->d;
+    if (d.loc_nb == nb) return SPTRSV_OK;
+    DeviceGuard g(p->device);
+    p->device_bytes -= d.loc_bytes;
+    free_local(d);
+    const HostSchedule &h = p->h;
+    const int32_t n = h.n;
+    const size_t nnz = size_t(p->nnz_off);
+    int st;
+    // the device-order factor back from the device (the caller's CSR is not kept)
+    std::vector<int32_t> rp, col;
+    if ((st = download(d.rp, size_t(n) + 1, rp)) || (st = download(d.col, nnz, col))) return st;
+    std::vector<int32_t> dev_of(n);
+    for (int32_t r = 0; r < n; ++r) dev_of[h.dev_perm[r]] = r;
+    // rows in (wavefront, id) order: counting sort by wavefront
+    std::vector<int32_t> lstart(size_t(h.nlevels) + 1, 0), ord(n);
+    for (int32_t v = 0; v < n; ++v) lstart[h.level[v] + 1]++;
+    for (int32_t l = 0; l < h.nlevels; ++l) lstart[l + 1] += lstart[l];
+    {
+        std::vector<int32_t> fill(lstart.begin(), lstart.end() - 1);
+        for (int32_t v = 0; v < n; ++v) ord[fill[h.level[v]]++] = v;
+    }
+    // every block keeps all of its rows' values in shared memory: cap the block size
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    const int32_t row_cap = int32_t((int64_t(optin) - 1024) / ((p->values & SPTRSV_VALUES_F64) ? 8 : 4));
+    if (int64_t(row_cap) * nb < int64_t(n))
+        return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the shared "
+                                        "memory of " + std::to_string(nb) + " blocks");
+    std::vector<int32_t> blk(n), lidx(n), cnt(nb, 0), load(nb, 0);
+    std::vector<std::pair<int32_t, int32_t>> tally;
+    int32_t cur = -1, cap = 0;
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = ord[t], l = h.level[v];
+        if (l != cur) {
+            cur = l;
+            std::fill(cnt.begin(), cnt.end(), 0);
+            const double w = double(lstart[l + 1] - lstart[l]);
+            cap = std::max<int32_t>(1, int32_t(std::ceil(w * kLocalSlack / nb)));
+        }
+        tally.clear();
+        const int32_t dr = dev_of[v];
+        for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q) {
+            const int32_t c = col[q], lc = h.level[c];
+            if (lc < l - 2) continue;
+            const int32_t w = lc == l - 1 ? 4 : 1, b = blk[c];
+            bool found = false;
+            for (auto &e : tally)
+                if (e.first == b) {
+                    e.second += w;
+                    found = true;
+                    break;
+                }
+            if (!found) tally.push_back({b, w});
+        }
+        int32_t best = -1, bestw = 0;
+        for (const auto &e : tally)
+            if (cnt[e.first] < cap && load[e.first] < row_cap &&
+                (e.second > bestw || (e.second == bestw && cnt[e.first] < cnt[best]))) {
+                best = e.first;
+                bestw = e.second;
+            }
+        if (best < 0) {
+            for (int32_t b = 0; b < nb; ++b)
+                if (load[b] < row_cap &&
+                    (best < 0 || cnt[b] < cnt[best] || (cnt[b] == cnt[best] && load[b] < load[best])))
+                    best = b;
+        }
+        blk[v] = best;
+        lidx[v] = load[best]++;
+        cnt[best]++;
+    }
+    std::vector<int32_t> bstart(size_t(nb) + 1, 0);
+    for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
+    // column ids in the block-local order: a parent of the same block -> its
+    // shared-memory slot -(position + 2), any other -> its original id
+    std::vector<int32_t> lperm(n), lrp(size_t(n) + 1, 0), lcol(nnz), src(nnz);
+    int32_t maxrows = 0;
+    for (int32_t v = 0; v < n; ++v) lperm[bstart[blk[v]] + lidx[v]] = v;
+    for (int32_t b = 0; b < nb; ++b) maxrows = std::max(maxrows, load[b]);
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = lperm[t], dr = dev_of[v];
+        int32_t o = lrp[t];
+        for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q, ++o) {
+            const int32_t c = col[q];
+            lcol[o] = blk[c] == blk[v] ? -(lidx[c] + 2) : c;
+            src[o] = q;
+        }
+        lrp[t + 1] = o;
+    }
+    int64_t bytes = 0;
+    if ((st = upload(lrp, &d.l_rp, &bytes)) || (st = upload(lcol, &d.l_col, &bytes)) ||
+        (st = upload(lperm, &d.l_perm, &bytes)) || (st = upload(bstart, &d.l_blk_row, &bytes)))
+        return st;
+    // values: a gather of the device-order arrays into the block-local order
+    auto regather = [&](auto *dval, auto *ddiag, auto **lval, auto **ldiag) -> int {
+        using V = std::remove_pointer_t<decltype(dval)>;
+        std::vector<V> hv, hd, ov(nnz), od(n);
+        int s2;
+        if ((s2 = download(dval, nnz, hv)) || (s2 = download(ddiag, size_t(n), hd))) return s2;
+        for (size_t q = 0; q < nnz; ++q) ov[q] = hv[size_t(src[q])];
+        for (int32_t t = 0; t < n; ++t) od[t] = hd[dev_of[lperm[t]]];
+        if ((s2 = upload(ov, lval, &bytes)) || (s2 = upload(od, ldiag, &bytes))) return s2;
+        return SPTRSV_OK;
+    };
+    if (d.val && (st = regather(d.val, d.dinv, &d.l_val, &d.l_dinv))) return st;
+    if (d.s32 && (st = regather(d.s32, d.dinv32, &d.l_s32, &d.l_dinv32))) return st;
+    d.loc_nb = nb;
+    d.loc_smem = size_t(maxrows) * size_t((p->values & SPTRSV_VALUES_F64) ? 8 : 4);
+    d.loc_bytes = bytes;
+    p->device_bytes += bytes;
+    return SPTRSV_OK;
+}
+
+template <typename T>
+void use_local(sptrsv_plan *p, SolveArgs<T> &a) {
+    a.rp = p->d.l_rp;
+    a.col = p->d.l_col;
+    a.perm = p->d.l_perm;
+    a.blk_row = p->d.l_blk_row;
+    if constexpr (std::is_same<T, double>::value) {
+        a.val = p->d.l_val;
+        a.dinv = p->d.l_dinv;
+    } else {
+        a.val = p->d.l_s32;
+        a.dinv = p->d.l_dinv32;
+    }
 }
 
 template <typename T>
@@ -317,6 +493,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
             if (!o.threads) o.threads = t.threads;
             if (!o.blocks_per_sm) o.blocks_per_sm = t.blocks_per_sm;
             if (!o.rhs_tile) o.rhs_tile = t.rhs_tile;
+            if (!o.eager_sum) o.eager_sum = t.eager_sum;
         }
     }
     c.sync = o.sync;
@@ -341,12 +518,27 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         c.lanes = o.lanes ? o.lanes : auto_lanes(p);
         if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
     }
+    if (o.eager_sum < 0 || o.eager_sum > 2) return fail(SPTRSV_ERR_ARG, "eager_sum must be 0, 1 or 2");
+    c.eager = o.eager_sum != SPTRSV_EAGER_OFF;
     c.threads = o.threads ? o.threads : 256;
-    if (c.threads < 32 || c.threads > 512 || c.threads % 32)
-        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
+    const int max_threads = c.sync == SPTRSV_SYNC_LOCAL ? 1024 : 512;
+    if (c.threads < 32 || c.threads > max_threads || c.threads % 32)
+        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL)");
     c.win = 0;
     c.smem = 0;
-    if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
+    if (c.sync == SPTRSV_SYNC_LOCAL) {
+        if (nrhs != 1 || c.rp) return fail(SPTRSV_ERR_ARG, "the block-local executor solves one right-hand side");
+        if (o.blocks_per_sm > 1) return fail(SPTRSV_ERR_ARG, "the block-local executor runs one block per SM");
+        int st = ensure_local(const_cast<sptrsv_plan *>(p), p->num_sms);
+        if (st) return st;
+        c.kind = 5;
+        c.smem = std::max<size_t>(16, p->d.loc_smem);   // sized for FP64 values (FP32 uses part)
+        int optin = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        if (c.smem > size_t(optin))
+            return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(p->d.loc_smem) +
+                                            " bytes per block exceed the shared memory of one SM");
+    } else if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
     else if (c.sync == SPTRSV_SYNC_GRID) {
         c.kind = wide_phases(p) ? 1 : 2;
         if (c.kind == 2 && c.rp) c.rp = false, c.lanes = auto_lanes(p);   // block executor: entry lanes
@@ -376,14 +568,14 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c.smem));
         if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     }
-    if (c.kind >= 3) {
+    if (c.kind == 3 || c.kind == 4) {
         c.grid = 1;
         return SPTRSV_OK;
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.threads, c.smem);
     if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, cudaGetErrorString(e));
-    int want = o.blocks_per_sm ? o.blocks_per_sm : std::min(per_sm, c.sync == SPTRSV_SYNC_GRID ? 1 : 2);
+    int want = o.blocks_per_sm ? o.blocks_per_sm : std::min(per_sm, c.sync == SPTRSV_SYNC_FLAGS ? 2 : 1);
     if (want > per_sm || want < 1)
         return fail(SPTRSV_ERR_LAUNCH, "persistent grid of " + std::to_string(want) +
                                            " blocks/SM cannot be co-resident (max " +
@@ -401,13 +593,13 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = (c.kind >= 3) ? 0 : 1;   // co-residency guaranteed or error
+    attr[0].val.cooperative = (c.kind == 3 || c.kind == 4) ? 0 : 1;   // co-residency guaranteed or error
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
     const int nph = int(p->h.phase_row.size()) - 1;
     const void *k = kernel_ptr<T>(c);
-    if (c.kind == 0 || c.kind == 2) {
+    if (c.kind == 0 || c.kind == 2 || c.kind == 5) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<Kern<T>>(const_cast<void *>(k)), args);
     } else if (c.kind == 4) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<StageKern<T>>(const_cast<void *>(k)), args, c.si, nph, c.win);
@@ -437,6 +629,7 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     a.step_blk = p->d.step_blk;
     a.blk_phase = p->d.blk_phase;
     a.phase_row = p->d.phase_row;
+    a.blk_row = nullptr;
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;
@@ -495,7 +688,8 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         if ((st = ensure_work(p, size_t(p->h.n) * size_t(nrhs) * sizeof(T) + 256))) return st;
         c.si.bdev = p->d.work;
     }
-    if (c.kind == 0) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
+    if (c.kind == 5) use_local(p, a);
+    if (c.kind == 0 || c.kind == 5) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
         CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
     }
     // zero the counters but keep the status word: a device error of an
@@ -553,13 +747,14 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     a.x64 = x;
     a.ldx64 = ld;
     a.rtol = o.refine_tol;
+    if (c.kind == 5) use_local(p, a);
     const int M = o.max_iters;
     for (int t = 0; t <= M + 1; ++t) {
         ra.sweep = t;
         k_residual<<<rgrid, 256, 0, s>>>(ra);
         CUDA_TRY(cudaGetLastError());
         if (t > M) break;
-        if (c.kind == 0) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));      // polled sweep: not-yet-computed
+        if (c.kind == 0 || c.kind == 5) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled sweep
         else CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, sizeof(unsigned long long), s));  // fresh barrier count
         a.refine = t == 0 ? 1 : 2;
         a.sweep = t;
@@ -635,6 +830,7 @@ void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
     o->threads = 0;
     o->timeout_s = 2.0;
     o->rhs_tile = 0;
+    o->eager_sum = SPTRSV_EAGER_AUTO;
 }
 
 int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
@@ -678,17 +874,25 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     if (nrhs >= 2)
         for (int tile : {4, 8, 16, 32})
             if (tile / 2 < nrhs) maps.push_back({tile, 0});
-    for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_CTA_REGS, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS}) {
+    for (int sync : {SPTRSV_SYNC_CTA, SPTRSV_SYNC_CTA_REGS, SPTRSV_SYNC_GRID, SPTRSV_SYNC_FLAGS, SPTRSV_SYNC_LOCAL}) {
         if ((sync == SPTRSV_SYNC_CTA || sync == SPTRSV_SYNC_CTA_REGS) && !small) continue;
+        if (sync == SPTRSV_SYNC_LOCAL && nrhs != 1) continue;
         for (auto [tile, lanes] : maps) {
-            for (int t : {128, 256, 512})
+            if (sync == SPTRSV_SYNC_LOCAL && tile != 1) continue;
+            for (int t : {128, 256, 512, 1024})
                 for (int bps : {1, 2}) {
+                    if (t > 512 && sync != SPTRSV_SYNC_LOCAL) continue;
                     const bool one_block = sync == SPTRSV_SYNC_CTA || sync == SPTRSV_SYNC_CTA_REGS;
-                    if (one_block && bps > 1) continue;
+                    if ((one_block || sync == SPTRSV_SYNC_LOCAL) && bps > 1) continue;
                     sptrsv_solve_opts c = o;
                     c.sync = sync; c.rhs_tile = tile; c.lanes = lanes; c.threads = t;
                     c.blocks_per_sm = one_block ? 0 : bps;
+                    c.eager_sum = SPTRSV_EAGER_ON;
                     cands.push_back(c);
+                    if ((sync == SPTRSV_SYNC_FLAGS || sync == SPTRSV_SYNC_LOCAL) && tile == 1 && lanes > 1) {
+                        c.eager_sum = SPTRSV_EAGER_OFF;
+                        cands.push_back(c);
+                    }
                 }
         }
     }
@@ -729,6 +933,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     m.threads = best_o.threads;
     m.blocks_per_sm = best_o.blocks_per_sm;
     m.rhs_tile = best_o.rhs_tile;
+    m.eager_sum = best_o.eager_sum;
     m.ms = best_t;
     if (best) *best = best_o;
     if (best_ms) *best_ms = best_t;

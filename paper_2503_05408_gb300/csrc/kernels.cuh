@@ -61,6 +61,7 @@ struct SolveArgs {
     const int32_t *__restrict__ step_blk;
     const int32_t *__restrict__ blk_phase;
     const int32_t *__restrict__ phase_row;
+    const int32_t *__restrict__ blk_row;   // block-local executor: rows of thread block b
     const T *b;
     T *x;
     int64_t ldb, ldx;
@@ -212,6 +213,22 @@ __device__ __forceinline__ T group_sum_width(T v, unsigned mask, int width) {
     return v;
 }
 
+// Lanes of every LANES-wide group of the warp in which no lane is set in
+// `blocking` (a warp-uniform mask): bit 0 of each group collects the OR of its
+// group, then the group leaders' bits are spread back over their groups.
+template <int LANES>
+__device__ __forceinline__ unsigned groups_clear(unsigned blocking) {
+    unsigned m = blocking;
+#pragma unroll
+    for (int s = 1; s < LANES; s <<= 1) m |= m >> s;
+    unsigned lead = 0;
+#pragma unroll
+    for (int g = 0; g < 32; g += LANES) lead |= 1u << g;
+    lead &= ~m;
+    if constexpr (LANES == 32) return lead ? 0xffffffffu : 0u;
+    else return lead * ((1u << LANES) - 1u);
+}
+
 // Eq. 2.1 for device row r: x[perm[r]] = (b[perm[r]] - sum_q val[q] x[col[q]]) / diag[r],
 // LANES lanes cooperating on the row, looping over the right-hand sides.
 template <typename T, int LANES>
@@ -273,6 +290,13 @@ template <>
 __device__ __forceinline__ bool is_sentinel<double>(double v) { return __double_as_longlong(v) == -1LL; }
 template <>
 __device__ __forceinline__ bool is_sentinel<float>(float v) { return __float_as_int(v) == -1; }
+
+template <typename T>
+__device__ __forceinline__ T all_ones();
+template <>
+__device__ __forceinline__ double all_ones<double>() { return __longlong_as_double(-1LL); }
+template <>
+__device__ __forceinline__ float all_ones<float>() { return __int_as_float(-1); }
 
 template <typename T>
 __device__ __forceinline__ T publishable(T v) {
@@ -501,11 +525,54 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
 // arrives, independently of the other groups: a warp holding 32/LANES rows
 // never makes a finished row wait for a slower sibling.  `has_row` is false for
 // groups past the end of the factor; they only take part in the votes.
+//
+// PRE (eager group sum): while a row waits, each poll round also reduces the
+// group's partial sum (the shuffles overlap the poll loads).  When a single
+// lane receives the row's last parents, that lane publishes presum - v*x: one
+// FMA after the arrival instead of FMA + log2(width) shuffle-adds.  It pays off
+// when a row's last parent arrives alone (rows with parents spread over many
+// wavefronts) and costs issue slots when all parents arrive together (stencils).
+//
+// LOCAL (block-local executor): a column id c <= -2 names a parent owned by
+// this thread block, whose value is polled in the block's shared-memory copy
+// xs[-c - 2] instead of global memory; -1 marks an empty register slot.  The
+// row's own value goes to xs[lrow] before the global store.
 // ----------------------------------------------------------------------------
-template <typename T, int LANES, int U>
+template <bool LOCAL>
+__device__ __forceinline__ bool has_entry(int c) { return LOCAL ? c != -1 : c >= 0; }
+
+template <typename T, bool LOCAL>
+__device__ __forceinline__ T fetch_polled(const T *xj, const T *xs, int c) {
+    if constexpr (LOCAL) {
+        if (c < 0) return reinterpret_cast<const volatile T *>(xs)[-c - 2];
+    }
+    return ld_poll(xj + c);
+}
+
+// Entries beyond the register tile (rows longer than U * LANES), consumed in
+// order while their values are ready.  Out of line: inlined into the poll loop,
+// its column/value loads were hoisted into every poll round.
+template <typename T, int LANES, bool PRE, bool LOCAL>
+__device__ __noinline__ void tail_step(const SolveArgs<T> &a, const T *xj, const T *xs, int end, int &q, T &acc,
+                                       T &ylast, bool &got) {
+    while (q < end) {
+        const int c = __ldg(a.col + q);
+        const T xc = fetch_polled<T, LOCAL>(xj, xs, c);
+        if (is_sentinel(xc)) break;
+        const T vq = __ldg(a.val + q);
+        acc -= vq * xc;
+        if constexpr (PRE) {
+            ylast -= vq * xc;
+            got = true;
+        }
+        q += LANES;
+    }
+}
+
+template <typename T, int LANES, int U, bool PRE, bool LOCAL = false>
 __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const RowRegs<T, U> &m, bool has_row,
                                                 int lane, unsigned gmask, unsigned long long &waits,
-                                                double &dm, double &xm) {
+                                                double &dm, double &xm, T *xs = nullptr, int lrow = 0) {
     constexpr unsigned kAll = 0xffffffffu;
     // the widest row of the warp sets the (warp-uniform) shuffle depth
     int width = has_row ? m.end - m.beg + 1 : 1;
@@ -520,58 +587,140 @@ __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const Row
             if (lane == 0) acc = (j == 0 ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb]) * m.dinv;
             T xv[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = m.c[u] >= 0 ? ld_poll(xj + m.c[u]) : T(0);
+            for (int u = 0; u < U; ++u) xv[u] = has_entry<LOCAL>(m.c[u]) ? fetch_polled<T, LOCAL>(xj, xs, m.c[u]) : T(0);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                if (m.c[u] >= 0) {
+                if (has_entry<LOCAL>(m.c[u])) {
                     if (is_sentinel(xv[u])) pend |= 1u << u;
                     else acc -= m.v[u] * xv[u];
                 }
             }
             if (pend) ++waits;
         }
-        bool published = !has_row;
+        if constexpr (LANES == 32) {
+            // one row per warp: poll until every parent landed, then reduce and publish
+            unsigned spins = 0;
+            long long t0 = 0;
+            while (__any_sync(kAll, pend != 0 || tail)) {
+                if (pend) {
+                    T xv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (pend & (1u << u)) xv[u] = fetch_polled<T, LOCAL>(xj, xs, m.c[u]);
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if ((pend & (1u << u)) && !is_sentinel(xv[u])) {
+                            acc -= m.v[u] * xv[u];
+                            pend &= ~(1u << u);
+                        }
+                } else if (tail) {
+                    T unused = T(0);
+                    bool g = false;
+                    tail_step<T, LANES, false, LOCAL>(a, xj, xs, m.end, q, acc, unused, g);
+                    tail = q < m.end;
+                }
+                if ((++spins & 63u) == 1) {
+                    if (spins == 1) {
+                        t0 = gtimer();
+                    } else {
+                        const bool expired = gtimer() - t0 > a.timeout_ns;
+                        if (__any_sync(kAll, ld_status(a.ctl) != 0 || expired)) {
+                            if (expired && lane == 0) raise_status(a.ctl, SPTRSV_ERR_TIMEOUT);
+                            return false;
+                        }
+                    }
+                }
+            }
+            if (has_row) {
+                const T y = group_sum_width<T, LANES>(acc, kAll, width);
+                if (lane == 0) {
+                    if constexpr (LOCAL) reinterpret_cast<volatile T *>(xs)[lrow] = publishable(y);
+                    st_pub(a.x + m.orow + (int64_t)j * a.ldx, publishable(y));
+                    if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+                }
+            }
+            continue;
+        }
+        // warp-uniform bookkeeping: `done` holds the lanes of groups that have
+        // published (or hold no row); one vote per poll round
+        const int lane32 = threadIdx.x & 31;
+        unsigned done = __ballot_sync(kAll, !has_row);
         unsigned spins = 0;
         long long t0 = 0;
+        // PRE: `presum` is the group's sum of everything accumulated before the
+        // last round (reduced once per round in which values landed, after the
+        // round's publications); `ylast` = presum minus this lane's arrivals of
+        // the last round, the row's value if this lane alone received some.
+        T presum = T(0), ylast = T(0);
+        bool got = false, refresh = false;
+        if constexpr (PRE && LANES > 1) presum = group_sum_width<T, LANES>(acc, kAll, width);
         // No lane ever blocks inside an iteration: a parent may be a row of this
         // same warp, published only at the vote below.
         while (true) {
             const unsigned busy = __ballot_sync(kAll, pend != 0 || tail);
-            const bool fin = !published && (busy & gmask) == 0;
-            if (__any_sync(kAll, fin)) {
-                T y = acc;
-                if constexpr (LANES > 1) y = group_sum_width<T, LANES>(y, kAll, width);
-                if (fin && lane == 0) {
-                    st_pub(a.x + m.orow + (int64_t)j * a.ldx, publishable(y));
-                    if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+            const unsigned fin = groups_clear<LANES>(busy | done);    // groups finishing now
+            if (fin) {
+                const bool mine = (fin >> lane32) & 1u;
+                if constexpr (LANES > 1) {
+                    bool single = false;
+                    T y = acc;
+                    if constexpr (PRE) {
+                        single = __popc(__ballot_sync(kAll, got) & gmask) == 1;
+                        if (__any_sync(kAll, mine && !single)) y = group_sum_width<T, LANES>(y, kAll, width);
+                    } else {
+                        y = group_sum_width<T, LANES>(y, kAll, width);
+                    }
+                    if (mine && (single ? got : lane == 0)) {
+                        if (single) y = ylast;
+                        if constexpr (LOCAL) reinterpret_cast<volatile T *>(xs)[lrow] = publishable(y);
+                        st_pub(a.x + m.orow + (int64_t)j * a.ldx, publishable(y));
+                        if (a.refine) refine_apply(a, m.orow, j, y, dm, xm);
+                    }
+                } else {
+                    if (mine) {
+                        if constexpr (LOCAL) reinterpret_cast<volatile T *>(xs)[lrow] = publishable(acc);
+                        st_pub(a.x + m.orow + (int64_t)j * a.ldx, publishable(acc));
+                        if (a.refine) refine_apply(a, m.orow, j, acc, dm, xm);
+                    }
                 }
-                published = published || fin;
+                done |= fin;
+            }
+            if constexpr (PRE && LANES > 1) {
+                if (refresh) presum = group_sum_width<T, LANES>(acc, kAll, width);
+                refresh = false;
             }
             if (busy == 0) break;
-            if (pend) {
-                // one more round of loads for this lane's missing parents; each is
-                // subtracted as soon as it lands
-                T xv[U];
+            T xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (pend & (1u << u)) xv[u] = fetch_polled<T, LOCAL>(xj, xs, m.c[u]);
+            // which parents landed: integer tests only
+            unsigned arrived = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if ((pend & (1u << u)) && !is_sentinel(xv[u])) arrived |= 1u << u;
+            pend &= ~arrived;
+            // An FP64 instruction holds the SM's FP64 pipe for the whole warp however
+            // few lanes are active, so a spinning warp issues none: the FP64 work of a
+            // round runs only when some lane's value landed.
+            const bool landed = __any_sync(kAll, arrived != 0);
+            if constexpr (PRE) {
+                got = arrived != 0;
+                ylast = presum;
+            }
+            if (landed) {
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (pend & (1u << u)) xv[u] = ld_poll(xj + m.c[u]);
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if ((pend & (1u << u)) && !is_sentinel(xv[u])) {
+                    if (arrived & (1u << u)) {
                         acc -= m.v[u] * xv[u];
-                        pend &= ~(1u << u);
+                        if constexpr (PRE) ylast -= m.v[u] * xv[u];
                     }
-            } else if (tail) {
-                // entries beyond the register tile (long rows), in order, while ready
-                while (q < m.end) {
-                    const int c = __ldg(a.col + q);
-                    const T xc = ld_poll(xj + c);
-                    if (is_sentinel(xc)) break;
-                    acc -= __ldg(a.val + q) * xc;
-                    q += LANES;
-                }
+            }
+            if (!pend && tail) {
+                tail_step<T, LANES, PRE, LOCAL>(a, xj, xs, m.end, q, acc, ylast, got);
                 tail = q < m.end;
             }
+            if constexpr (PRE) refresh = __any_sync(kAll, got);
             if ((++spins & 63u) == 1) {                      // warp-uniform bound on the wait
                 if (spins == 1) {
                     t0 = gtimer();
@@ -597,7 +746,7 @@ __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const Row
 // warps advance together (warp-uniform loop, per-group publication); right-hand-
 // side tiles run one row per group.
 // ----------------------------------------------------------------------------
-template <typename T, int LANES, int U, bool RP>
+template <typename T, int LANES, int U, bool RP, bool PRE = false>
 __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
     constexpr int RPW = 32 / LANES;
     const int lane32 = threadIdx.x & 31;
@@ -628,10 +777,57 @@ __global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
             r = rb + grp;
             if (r + 2 * G < a.n) load_meta(a, r + 2 * G, nn);
             if (r + G < a.n) load_entries<T, LANES, U, RP>(a, lane, nxt);
-            if (!row_exec_polled<T, LANES, U>(a, cur, r < a.n, lane, mask, waits, dm, xm)) break;
+            if (!row_exec_polled<T, LANES, U, PRE>(a, cur, r < a.n, lane, mask, waits, dm, xm)) break;
             cur = nxt;
             nxt = nn;
         }
+    }
+    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
+// ----------------------------------------------------------------------------
+// Block-local executor (SPTRSV_SYNC_LOCAL).  The plan's rows are partitioned
+// over the thread blocks of a persistent grid so that most dependency edges,
+// in particular the edge to each row's last-finishing parent, join rows of the
+// same block (the locality GrowLocal seeks for CPU cores, Sec. 3).  A block
+// keeps the values of all of its rows in shared memory (all-ones NaN until
+// written): parents owned by the block are polled there (tens of cycles), the
+// others in global memory (an L2 round trip).  Rows are listed per block in
+// (wavefront, id) order and dealt round-robin to the block's row groups, so the
+// smallest unfinished (wavefront, id) row always has its owner at it: with all
+// blocks co-resident (cooperative launch) the walk cannot deadlock.
+// ----------------------------------------------------------------------------
+template <typename T, int LANES, int U, bool PRE>
+__global__ void __launch_bounds__(1024, 1) k_local(SolveArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    constexpr int RPW = 32 / LANES;
+    const int lane32 = threadIdx.x & 31;
+    const int grp = lane32 / LANES, lane = lane32 % LANES;
+    const unsigned mask = group_mask<LANES>(lane32);
+    const int r0 = a.blk_row[blockIdx.x], nr = a.blk_row[blockIdx.x + 1] - r0;
+    if (refine_skip(a)) return;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) xs[i] = all_ones<T>();
+    __syncthreads();
+    unsigned long long waits = 0;
+    double dm = 0.0, xm = 0.0;
+    const int wbase = (threadIdx.x >> 5) * RPW;                 // the warp's first block row
+    const int G = (blockDim.x >> 5) * RPW;
+    RowRegs<T, U> cur, nxt, nn;
+    int lr = wbase + grp;
+    if (lr < nr) {
+        load_meta(a, r0 + lr, cur);
+        load_entries<T, LANES, U, false>(a, lane, cur);
+    }
+    if (lr + G < nr) load_meta(a, r0 + lr + G, nxt);
+    for (int rb = wbase; rb < nr; rb += G) {                    // warp-uniform
+        lr = rb + grp;
+        if (lr + 2 * G < nr) load_meta(a, r0 + lr + 2 * G, nn);
+        if (lr + G < nr) load_entries<T, LANES, U, false>(a, lane, nxt);
+        if (!row_exec_polled<T, LANES, U, PRE, true>(a, cur, lr < nr, lane, mask, waits, dm, xm, xs, lr)) break;
+        cur = nxt;
+        nxt = nn;
     }
     if (waits) atomicAdd(&a.ctl->flag_waits, waits);
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);

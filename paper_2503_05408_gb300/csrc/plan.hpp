@@ -63,6 +63,16 @@ struct DeviceBuffers {
     uint32_t *flags = nullptr;    // n ready flags holding the solve epoch
     void *work = nullptr;         // refinement / internal vectors (grown on demand)
     size_t work_bytes = 0;
+    // block-local executor layout (built on first use for loc_nb thread blocks):
+    // rows block-major, each block's rows in (wavefront, id) order; a column id
+    // c >= 0 is an original row id (parent of another block), c <= -2 names the
+    // parent at position -c - 2 of the same block
+    int32_t loc_nb = 0;           // 0 = not built
+    size_t loc_smem = 0;          // shared memory of the largest block (its rows' values)
+    int64_t loc_bytes = 0;
+    int32_t *l_rp = nullptr, *l_col = nullptr, *l_perm = nullptr, *l_blk_row = nullptr;
+    double *l_val = nullptr, *l_dinv = nullptr;
+    float *l_s32 = nullptr, *l_dinv32 = nullptr;
 };
 
 }  // namespace sptrsv
@@ -82,7 +92,7 @@ struct sptrsv_plan {
     // call being served is selected by sptrsv_solve before it picks a configuration
     struct TunedCfg {
         bool valid = false;
-        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0, rhs_tile = 0;
+        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0, rhs_tile = 0, eager_sum = 0;
         double ms = 0.0;
     };
     TunedCfg tuned[16];

@@ -59,7 +59,7 @@ SMALL = {
 
 
 @pytest.mark.parametrize("name", sorted(SMALL))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local"])
 @pytest.mark.parametrize("lanes", [1, 4, 32])
 def test_f64_levels_parity(name, sync, lanes):
     A = SMALL[name]()
@@ -73,8 +73,27 @@ def test_f64_levels_parity(name, sync, lanes):
         assert rep["barriers"] == plan.stats()["supersteps"] - 1
 
 
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("lanes", [2, 8, 32])
+@pytest.mark.parametrize("eager", [1, 2])
+@pytest.mark.parametrize("threads", [128, 512])
+@pytest.mark.parametrize("sync", ["flags", "local"])
+def test_polled_eager_sum_parity(name, lanes, eager, threads, sync):
+    # polled executors, entry-split lanes, with and without the eager group sum;
+    # dense_rows (40 entries per row) also runs the non-blocking long-row tail
+    A = SMALL[name]()
+    nrhs = 2 if sync == "flags" else 1
+    xs, b = W.manufactured_rhs(A, nrhs, seed=17)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A, mode="levels")
+    x, rep = solve_gpu(plan, b, sync=sync, lanes=lanes, rhs_tile=1, eager_sum=eager, threads=threads,
+                       blocks_per_sm=1)
+    assert rep["status"] == 0 and rep["lanes"] == lanes
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
 @pytest.mark.parametrize("name", ["lap2d_64x64", "er_30k", "nb_20k", "banded_20k"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local"])
 @pytest.mark.parametrize("k", [1, 8, 152])
 def test_f64_growlocal_parity(name, sync, k):
     A = SMALL[name]()
@@ -119,7 +138,7 @@ def test_f32_solve():
         xs, b = W.manufactured_rhs(A, 1, seed=14)
         xo = oracle.solve(A, b)
         plan = sp.Plan(A)
-        for sync in ("grid", "flags", "cta"):
+        for sync in ("grid", "flags", "cta", "local"):
             x, rep = solve_gpu(plan, b, dtype=torch.float32, sync=sync)
             assert oracle.rel_error(x, xo) <= 1e-4
 
@@ -129,7 +148,7 @@ def test_edge_sizes(n):
     A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
     b = np.ones((n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta", "cta_regs"):
+    for sync in ("grid", "flags", "cta", "cta_regs", "local"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert np.allclose(x[:, 0], 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)
 
@@ -139,7 +158,7 @@ def test_diagonal_only_is_one_superstep():
     A.val[:] = np.linspace(0.5, 2.0, A.n)
     b = np.random.default_rng(0).standard_normal((A.n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta"):
+    for sync in ("grid", "flags", "cta", "local"):
         x, rep = solve_gpu(plan, b, sync=sync)
         # x = b * (1/d): the reciprocal is rounded once on the host, so at most two roundings
         assert np.max(np.abs(x[:, 0] - b[:, 0] / A.val) / np.abs(b[:, 0] / A.val)) <= 4.5e-16
@@ -170,9 +189,32 @@ def test_full_size_configs_f64(cfg):
     xo = oracle.solve(A, b)
     assert oracle.rel_error(xo, xs) < 1e-13
     plan = sp.Plan(A)
-    for sync in ("grid", "flags"):
+    for sync in ("grid", "flags", "local"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("lanes", [32, 8])
+def test_local_executor_full_block(name, lanes):
+    # 1024 threads per block (32 warps) on the block-local executor
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=19)
+    plan = sp.Plan(A)
+    x, rep = solve_gpu(plan, b, sync="local", lanes=lanes, threads=1024)
+    assert rep["status"] == 0 and rep["threads"] == 1024
+    assert oracle.rel_error(x, oracle.solve(A, b)) <= F64_TOL
+
+
+def test_local_executor_rejects_several_rhs():
+    A = W.laplace2d_lower(4096, 64)
+    xs, b = W.manufactured_rhs(A, 2, seed=18)
+    plan = sp.Plan(A)
+    with pytest.raises(sp.SptrsvError) as e:
+        solve_gpu(plan, b, sync="local")
+    assert e.value.status == sp.ERR_ARG
+    x, rep = solve_gpu(plan, b[:, :1], sync="local")            # the plan stays usable
+    assert oracle.rel_error(x, oracle.solve(A, b[:, :1])) <= F64_TOL
 
 
 # ------------------------------------------------------------ FP32 + FP64 refinement
@@ -186,9 +228,11 @@ REFINE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(REFINE_CASES))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local"])
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_refine_parity(name, sync, nrhs):
+    if sync == "local" and nrhs > 1:
+        pytest.skip("the block-local executor solves one right-hand side")
     A = REFINE_CASES[name]()
     xs, b = W.manufactured_rhs(A, nrhs, seed=21)
     xo = oracle.solve(A, b)
@@ -241,7 +285,7 @@ def test_full_size_random_refine():
     A, xs, b = W.config_random_1m()
     xo = oracle.solve(A, b)
     plan = sp.Plan(A)
-    for sync in ("flags", "grid"):
+    for sync in ("flags", "grid", "local"):
         x, rep = solve_gpu(plan, b, sync=sync, precision="f32_refine")
         assert oracle.rel_error(x, xo) <= F64_TOL
 
