@@ -320,6 +320,7 @@ __device__ __forceinline__ void st_pub(float *p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+
 template <typename T, int U>
 struct RowRegs {
     int beg, end, orow;
@@ -335,6 +336,12 @@ __device__ __forceinline__ void load_meta(const SolveArgs<T> &a, int r, RowRegs<
     m.end = __ldg(a.rp + r + 1);
     m.orow = __ldg(a.perm + r);
     m.dinv = __ldg(a.dinv + r);
+}
+
+// The scaled right-hand side b_i / A_ii of column 0 (lane 0 of the group)
+template <typename T, int U>
+__device__ __forceinline__ T scaled_b0(const SolveArgs<T> &, const RowRegs<T, U> &m) {
+    return m.b0 * m.dinv;
 }
 
 // RP (right-hand-side parallel tile): every lane of the group holds the same U
@@ -541,6 +548,8 @@ __device__ __forceinline__ bool row_exec(const SolveArgs<T> &a, const RowRegs<T,
 template <bool LOCAL>
 __device__ __forceinline__ bool has_entry(int c) { return LOCAL ? c != -1 : c >= 0; }
 
+
+
 template <typename T, bool LOCAL>
 __device__ __forceinline__ T fetch_polled(const T *xj, const T *xs, int c) {
     if constexpr (LOCAL) {
@@ -569,10 +578,108 @@ __device__ __noinline__ void tail_step(const SolveArgs<T> &a, const T *xj, const
     }
 }
 
+// ----------------------------------------------------------------------------
+// One row per warp, lanes split its entries (one right-hand side).  FP64
+// instructions are few and late: on this part a warp-wide FP64 instruction
+// holds the SM's FP64 pipe for about 19 cycles however few lanes are active, so
+// the parents' values are collected first (integer tests only) and the row is
+// finished with one FMA per lane and the group reduction.
+//   publish_row: shared-memory copy (block-local executor), then the global value.
+// ----------------------------------------------------------------------------
+template <typename T, bool LOCAL>
+__device__ __forceinline__ void publish_row(const SolveArgs<T> &a, int orow, T y, T *xs, int lrow, double &dm,
+                                            double &xm) {
+    if constexpr (LOCAL) reinterpret_cast<volatile T *>(xs)[lrow] = publishable(y);
+    st_pub(a.x + orow, publishable(y));
+    if (a.refine) refine_apply(a, orow, 0, y, dm, xm);
+}
+
+// Bounded-wait bookkeeping shared by the one-row loops: every 64 rounds, give up
+// if another block recorded an error or the wait exceeded the limit.
+__device__ __forceinline__ bool wait_ok(const Ctl *ctl, long long timeout_ns, unsigned &spins, long long &t0,
+                                        int lane) {
+    if ((++spins & 63u) != 1) return true;
+    if (spins == 1) {
+        t0 = gtimer();
+        return true;
+    }
+    const bool expired = gtimer() - t0 > timeout_ns;
+    if (__any_sync(0xffffffffu, ld_status(ctl) != 0 || expired)) {
+        if (expired && lane == 0) raise_status(const_cast<Ctl *>(ctl), SPTRSV_ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// Polled form (flags executor, and the block-local executor without row
+// barriers): every pending parent is polled each round.  PRE: once a single
+// lane still waits, the others' sum is reduced; when its value lands that lane
+// publishes presum - v*x without the reduction.
+template <typename T, bool PRE, bool LOCAL>
+__device__ __forceinline__ bool row_exec_lean(const SolveArgs<T> &a, const RowRegs<T, 1> &m, bool has_row, int lane,
+                                              unsigned long long &waits, double &dm, double &xm, T *xs, int lrow) {
+    constexpr unsigned kAll = 0xffffffffu;
+    int width = has_row ? m.end - m.beg + 1 : 1;
+    width = __reduce_max_sync(kAll, width);
+    const int c = m.c[0];
+    T acc = (has_row && lane == 0) ? scaled_b0(a, m) : T(0);
+    T x = T(0);
+    bool pend = false;
+    int q = has_row ? m.beg + lane + 32 : 0;
+    bool tail = has_row && q < m.end;
+    if (has_row && has_entry<LOCAL>(c)) {
+        x = fetch_polled<T, LOCAL>(a.x, xs, c);
+        pend = is_sentinel(x);
+        if (pend) ++waits;
+    }
+    bool single = false, last = false;
+    T presum = T(0);
+    unsigned spins = 0;
+    long long t0 = 0;
+    while (__any_sync(kAll, pend || tail)) {
+        if constexpr (PRE) {
+            if (!single) {
+                const unsigned pl = __ballot_sync(kAll, pend || tail);
+                if (__popc(pl) == 1 && !__any_sync(kAll, tail)) {
+                    // reduce everything but the last outstanding parent while it is awaited
+                    const T part = pend ? acc : acc - m.v[0] * x;
+                    presum = group_sum_width<T, 32>(part, kAll, width);
+                    single = true;
+                    last = pend;
+                }
+            }
+        }
+        if (pend) {
+            const T t = fetch_polled<T, LOCAL>(a.x, xs, c);
+            if (!is_sentinel(t)) {
+                x = t;
+                pend = false;
+            }
+        } else if (tail) {
+            T unused = T(0);
+            bool g = false;
+            tail_step<T, 32, false, LOCAL>(a, a.x, xs, m.end, q, acc, unused, g);
+            tail = q < m.end;
+        }
+        if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
+    }
+    if (!has_row) return true;
+    if (single) {
+        if (last) publish_row<T, LOCAL>(a, m.orow, presum - m.v[0] * x, xs, lrow, dm, xm);
+    } else {
+        const T y = group_sum_width<T, 32>(acc - m.v[0] * x, kAll, width);
+        if (lane == 0) publish_row<T, LOCAL>(a, m.orow, y, xs, lrow, dm, xm);
+    }
+    return true;
+}
+
 template <typename T, int LANES, int U, bool PRE, bool LOCAL = false>
 __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const RowRegs<T, U> &m, bool has_row,
                                                 int lane, unsigned gmask, unsigned long long &waits,
                                                 double &dm, double &xm, T *xs = nullptr, int lrow = 0) {
+    if constexpr (LANES == 32 && U == 1 && !LOCAL) {
+        if (a.nrhs == 1) return row_exec_lean<T, PRE, LOCAL>(a, m, has_row, lane, waits, dm, xm, xs, lrow);
+    }
     constexpr unsigned kAll = 0xffffffffu;
     // the widest row of the warp sets the (warp-uniform) shuffle depth
     int width = has_row ? m.end - m.beg + 1 : 1;
@@ -584,7 +691,7 @@ __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const Row
         int q = has_row ? m.beg + lane + U * LANES : 0;     // next entry beyond the register tile
         bool tail = has_row && q < m.end;
         if (has_row) {
-            if (lane == 0) acc = (j == 0 ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb]) * m.dinv;
+            if (lane == 0) acc = j == 0 ? scaled_b0(a, m) : a.b[m.orow + (int64_t)j * a.ldb] * m.dinv;
             T xv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) xv[u] = has_entry<LOCAL>(m.c[u]) ? fetch_polled<T, LOCAL>(xj, xs, m.c[u]) : T(0);
