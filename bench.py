@@ -648,7 +648,7 @@ def run_serve_reference(args):
     return 0
 
 
-SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta"}
+SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta", "cta_regs": "cta_regs", "local": "local"}
 
 
 def main():
