@@ -91,6 +91,22 @@ def dist_info():
     return world, rank, local
 
 
+def world_max(values, dist, device):
+    """Max over ranks of per-rank timings (every rank calls it; identity without a process group)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    timed by the slowest rank (weak scaling: per-rank work is fixed)."""
+    return units_per_rank * world / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -321,14 +337,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     e2e_total = sum(e0.elapsed_time(e1) * 1e-3 for e0, e1 in ev2)
-    if dist:
-        t = torch.tensor([dev_total, e2e_total], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_total, e2e_total = float(t[0]), float(t[1])
+    dev_total, e2e_total = world_max([dev_total, e2e_total], dist, f"cuda:{local}")
 
     nnz_step = A.nnz * nrhs
-    value = nnz_step * args.steps * world / dev_total
-    e2e_value = nnz_step * args.steps * world / e2e_total
+    value = replica_throughput(nnz_step * args.steps, world, dev_total)
+    e2e_value = replica_throughput(nnz_step * args.steps, world, e2e_total)
     mean_s = dev_total / args.steps
     # HBM bytes of one sweep: FP64 values for a plain solve, FP32 values (hi) for a refinement sweep
     bytes_launch = algorithmic_bytes(A.n, A.nnz, nrhs, 8 if precision == "f64" else 4,
