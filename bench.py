@@ -78,6 +78,7 @@ def parse_args():
     ap.add_argument("--lanes", type=int, default=None)
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--blocks-per-sm", type=int, default=None)
+    ap.add_argument("--rhs-tile", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -279,7 +280,8 @@ def run_ours(args):
         b = torch.from_numpy(np.ascontiguousarray(b_np.T)).to(f"cuda:{local}", tdtype).T
     x = torch.empty_strided(b.shape, b.stride(), dtype=tdtype, device=b.device)
     precision = args.precision or spec.get("precision", "f64")
-    opts = dict(sync=args.sync, lanes=args.lanes, threads=args.threads, blocks_per_sm=args.blocks_per_sm)
+    opts = dict(sync=args.sync, lanes=args.lanes, threads=args.threads, blocks_per_sm=args.blocks_per_sm,
+                rhs_tile=args.rhs_tile)
     opts = {k: v for k, v in opts.items() if v is not None}
     opts["precision"] = precision
     if "sync" not in opts:

@@ -54,6 +54,7 @@ __device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;
+    a.brs = a.xrs = 1;
     a.ctl = nullptr;
     a.flags = nullptr;
     a.epoch = 0;
@@ -62,6 +63,7 @@ __device__ __forceinline__ SolveArgs<T> item_args(const BatchItem &it, const T *
     a.sweep = 0;
     a.x64 = nullptr;
     a.ldx64 = 0;
+    a.x64rs = 1;
     a.rtol = 0.0;
     a.lnorm = it.lnorm;
     return a;

@@ -85,6 +85,8 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
     int64_t bytes = 0;
     int st;
     DeviceBuffers &d = p->d;
+    p->max_row_off = 0;
+    for (int32_t r = 0; r < n; ++r) p->max_row_off = std::max(p->max_row_off, rp[r + 1] - rp[r]);
     if ((st = upload(rp, &d.rp, &bytes))) return st;
     if ((st = upload(col, &d.col, &bytes))) return st;
     // rows scaled by their diagonal: x_i = b_i / A_ii - sum_j (A_ij / A_ii) x_j
@@ -172,8 +174,19 @@ bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lane
 bool rp_ok(int tile) { return tile == 4 || tile == 8 || tile == 16 || tile == 32; }
 
 template <typename T, bool RP>
-Kern<T> flags_kernel(int lanes, bool pre) {
+Kern<T> flags_kernel(int lanes, bool pre, bool short_rows = false) {
     if constexpr (RP) {
+        // rows of at most 4 off-diagonal entries: a 4-entry register tile, fewer
+        // registers, twice the resident warps
+        if (short_rows) {
+            switch (lanes) {
+                case 4: return k_flags<T, 4, 4, true>;
+                case 8: return k_flags<T, 8, 4, true>;
+                case 16: return k_flags<T, 16, 4, true>;
+                case 32: return k_flags<T, 32, 4, true>;
+                default: return nullptr;
+            }
+        }
         switch (lanes) {
             case 4: return k_flags<T, 4, kRpTile, true>;
             case 8: return k_flags<T, 8, kRpTile, true>;
@@ -279,6 +292,7 @@ struct LaunchCfg {
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
     bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
     bool eager;        // polled executor: eager group sum (SPTRSV_EAGER_ON)
+    bool short_rows;   // every row has at most 4 off-diagonal entries
     size_t smem;
 };
 
@@ -308,7 +322,7 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
         return c.win ? reinterpret_cast<const void *>(stage_kernel<T, true, RP>(c.lanes))
                      : reinterpret_cast<const void *>(stage_kernel<T, false, RP>(c.lanes));
     switch (c.kind) {
-        case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager));
+        case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager, c.short_rows));
         case 5: return RP ? nullptr : reinterpret_cast<const void *>(local_kernel<T>(c.lanes, c.eager));
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
         case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
@@ -526,6 +540,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL)");
     c.win = 0;
     c.smem = 0;
+    c.short_rows = p->max_row_off <= 4;
     if (c.sync == SPTRSV_SYNC_LOCAL) {
         if (nrhs != 1 || c.rp) return fail(SPTRSV_ERR_ARG, "the block-local executor solves one right-hand side");
         if (o.blocks_per_sm > 1) return fail(SPTRSV_ERR_ARG, "the block-local executor runs one block per SM");
@@ -633,6 +648,7 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;
+    a.brs = a.xrs = 1;
     a.ctl = reinterpret_cast<Ctl *>(p->d.counters);
     a.flags = p->d.flags;
     a.epoch = 0;
@@ -641,6 +657,7 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     a.sweep = 0;
     a.x64 = nullptr;
     a.ldx64 = 0;
+    a.x64rs = 1;
     a.rtol = 0.0;
     a.lnorm = p->lnorm;
     return a;
@@ -689,13 +706,35 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         c.si.bdev = p->d.work;
     }
     if (c.kind == 5) use_local(p, a);
-    if (c.kind == 0 || c.kind == 5) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
+    // right-hand-side tiles on the grid executors: internal row-major copies of b
+    // and x (original row order), so a tile gathers a parent's values in one load
+    const bool rows = c.rp && nrhs > 1 && (c.kind == 0 || c.kind == 1) && p->h.n > 0;
+    T *xr = nullptr;
+    const dim3 tgrid((p->h.n + 31) / 32, (nrhs + 31) / 32), tblock(32, 8);
+    if (rows) {
+        const size_t vec = (size_t(p->h.n) * size_t(nrhs) * sizeof(T) + 255) & ~size_t(255);
+        if ((st = ensure_work(p, 2 * vec + 256))) return st;
+        T *br = static_cast<T *>(p->d.work);
+        xr = reinterpret_cast<T *>(static_cast<char *>(p->d.work) + vec);
+        k_to_rows<T><<<tgrid, tblock, 0, s>>>(static_cast<const T *>(b), ld, br, c.kind == 0 ? xr : nullptr,
+                                               p->h.n, nrhs);
+        CUDA_TRY(cudaGetLastError());
+        a.b = br;
+        a.x = xr;
+        a.ldb = a.ldx = 1;
+        a.brs = a.xrs = nrhs;
+    } else if (c.kind == 0 || c.kind == 5) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
         CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
     }
     // zero the counters but keep the status word: a device error of an
     // asynchronous solve stays visible until a report reads and clears it
     CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
-    return launch<T>(p, c, a, s);
+    if ((st = launch<T>(p, c, a, s))) return st;
+    if (rows) {
+        k_to_cols<T><<<tgrid, tblock, 0, s>>>(xr, static_cast<T *>(x), ld, p->h.n, nrhs);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return SPTRSV_OK;
 }
 
 
@@ -714,11 +753,24 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     const int32_t n = p->h.n;
     const size_t vec = size_t(n) * size_t(nrhs) * sizeof(float);
     const size_t vpad = (vec + 255) & ~size_t(255);
-    if ((st = ensure_work(p, 3 * vpad + 256))) return st;
-    float *r32 = static_cast<float *>(p->d.work);
-    float *d32 = reinterpret_cast<float *>(static_cast<char *>(p->d.work) + vpad);
-    c.si.bdev = static_cast<char *>(p->d.work) + 2 * vpad;       // staged walk: b in device order
+    // right-hand-side tiles on the grid executors: residual, correction, b and the
+    // FP64 iterate all kept row-major in internal buffers (a row's right-hand
+    // sides in one or two lines; b and x change layout once, at the ends)
+    const bool rows = c.rp && nrhs > 1 && (c.kind == 0 || c.kind == 1) && n > 0;
+    const size_t dpad = rows ? ((size_t(n) * size_t(nrhs) * sizeof(double) + 255) & ~size_t(255)) : 0;
+    if ((st = ensure_work(p, 3 * vpad + 2 * dpad + 256))) return st;
+    char *wk = static_cast<char *>(p->d.work);
+    float *r32 = reinterpret_cast<float *>(wk);
+    float *d32 = reinterpret_cast<float *>(wk + vpad);
+    c.si.bdev = wk + 2 * vpad;                                   // staged walk: b in device order
+    double *br = rows ? reinterpret_cast<double *>(wk + 3 * vpad) : nullptr;
+    double *xr = rows ? reinterpret_cast<double *>(wk + 3 * vpad + dpad) : nullptr;
+    const dim3 tgrid((n + 31) / 32, (nrhs + 31) / 32), tblock(32, 8);
     CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, offsetof(Ctl, status), s));
+    if (rows) {
+        k_to_rows<double><<<tgrid, tblock, 0, s>>>(b, ld, br, nullptr, n, nrhs);
+        CUDA_TRY(cudaGetLastError());
+    }
     ResidualArgs ra;
     ra.n = n;
     ra.nrhs = nrhs;
@@ -729,23 +781,34 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     ra.dhi = p->d.diag_hi;
     ra.dlo = p->d.diag_lo;
     ra.perm = p->d.perm;
-    ra.b = b;
-    ra.ldb = ld;
-    ra.x = x;
-    ra.ldx = ld;
+    ra.b = rows ? br : b;
+    ra.ldb = rows ? 1 : ld;
+    ra.b_rs = rows ? nrhs : 1;
+    ra.x = rows ? xr : x;
+    ra.ldx = rows ? 1 : ld;
+    ra.x_rs = rows ? nrhs : 1;
     ra.r32 = r32;
+    ra.r_rs = rows ? nrhs : 1;
+    ra.r_cs = rows ? 1 : n;
     ra.ctl = reinterpret_cast<Ctl *>(p->d.counters);
     ra.dtol = o.refine_tol;
     const int rgrid = std::max(1, std::min(4 * p->num_sms, (n + 255) / 256));
     SolveArgs<float> a = base_args<float>(p, p->d.s32, p->d.dinv32);
     a.nrhs = nrhs;
     a.b = r32;
-    a.ldb = n;
     a.x = d32;
-    a.ldx = n;
+    if (rows) {
+        a.ldb = a.ldx = 1;
+        a.brs = a.xrs = nrhs;
+        a.x64 = xr;
+        a.ldx64 = 1;
+        a.x64rs = nrhs;
+    } else {
+        a.ldb = a.ldx = n;
+        a.x64 = x;
+        a.ldx64 = ld;
+    }
     a.timeout_ns = (long long)(o.timeout_s * 1e9);
-    a.x64 = x;
-    a.ldx64 = ld;
     a.rtol = o.refine_tol;
     if (c.kind == 5) use_local(p, a);
     const int M = o.max_iters;
@@ -759,6 +822,10 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
         a.refine = t == 0 ? 1 : 2;
         a.sweep = t;
         if ((st = launch<float>(p, c, a, s))) return st;
+    }
+    if (rows) {
+        k_to_cols<double><<<tgrid, tblock, 0, s>>>(xr, x, ld, n, nrhs);
+        CUDA_TRY(cudaGetLastError());
     }
     return SPTRSV_OK;
 }

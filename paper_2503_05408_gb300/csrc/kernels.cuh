@@ -65,6 +65,7 @@ struct SolveArgs {
     const T *b;
     T *x;
     int64_t ldb, ldx;
+    int64_t brs, xrs;   // row strides of b and x: 1 = column-major; nrhs = row-major (tiles only)
     Ctl *ctl;
     uint32_t *flags;
     uint32_t epoch;
@@ -74,7 +75,7 @@ struct SolveArgs {
     // (refine == 1: first sweep, x64 = d) and tracks max |d| and max |x64|.
     int32_t refine, sweep;
     double *x64;
-    int64_t ldx64;
+    int64_t ldx64, x64rs;   // column and row strides of x64
     double rtol, lnorm;              // backward-error test: r <= rtol * (lnorm |x| + |b|)
 };
 
@@ -107,13 +108,21 @@ __device__ __forceinline__ bool refine_skip(const SolveArgs<T> &a) {
 }
 
 // Epilogue of a correction: x64 += d in FP64 (lane 0 of the row's group).
+// The running maxima compare bit patterns of non-negative doubles as integers
+// (same order), keeping FP64-pipe work to the conversion and the update.
+__device__ __forceinline__ double max_abs_bits(double m, double v) {
+    const unsigned long long a = __double_as_longlong(m), b = __double_as_longlong(v) & 0x7fffffffffffffffULL;
+    return __longlong_as_double(a > b ? a : b);
+}
+
 template <typename T>
 __device__ __forceinline__ void refine_apply(const SolveArgs<T> &a, int orow, int j, T d, double &dm, double &xm) {
-    double *px = a.x64 + orow + (int64_t)j * a.ldx64;
-    const double xn = (a.refine == 1 ? 0.0 : *px) + double(d);
+    double *px = a.x64 + (int64_t)orow * a.x64rs + (int64_t)j * a.ldx64;
+    const double dd = double(d);
+    const double xn = (a.refine == 1 ? 0.0 : *px) + dd;
     *px = xn;
-    dm = fmax(dm, fabs(double(d)));
-    xm = fmax(xm, fabs(xn));
+    dm = max_abs_bits(dm, dd);
+    xm = max_abs_bits(xm, xn);
 }
 
 // Block-reduce the per-thread maxima and fold them into the sweep's slots.
@@ -349,7 +358,7 @@ __device__ __forceinline__ T scaled_b0(const SolveArgs<T> &, const RowRegs<T, U>
 // Otherwise lanes split the row's entries and one lane owns the result.
 template <typename T, int LANES, int U, bool RP = false>
 __device__ __forceinline__ void load_entries(const SolveArgs<T> &a, int lane, RowRegs<T, U> &m) {
-    if constexpr (RP) m.b0 = (lane < a.nrhs) ? a.b[m.orow + (int64_t)lane * a.ldb] : T(0);
+    if constexpr (RP) m.b0 = (lane < a.nrhs) ? a.b[(int64_t)m.orow * a.brs + (int64_t)lane * a.ldb] : T(0);
     else m.b0 = (lane == 0) ? a.b[m.orow] : T(0);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -394,14 +403,14 @@ __device__ __forceinline__ bool row_exec_rp(const SolveArgs<T> &a, const RowRegs
     bool ok = true;
     for (int j = lane; j < a.nrhs && ok; j += LANES) {
         const T *xj = a.x + (int64_t)j * a.ldx;
-        const T bj = (j == lane) ? m.b0 : a.b[m.orow + (int64_t)j * a.ldb];
+        const T bj = (j == lane) ? m.b0 : a.b[(int64_t)m.orow * a.brs + (int64_t)j * a.ldb];
         T xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (m.c[u] >= 0) {
                 if constexpr (MODE == 2) xv[u] = xs[(m.c[u] & (win - 1)) + j * win];
-                else if constexpr (MODE == 1) xv[u] = ld_poll(xj + m.c[u]);
-                else xv[u] = xj[m.c[u]];
+                else if constexpr (MODE == 1) xv[u] = ld_poll(xj + (int64_t)m.c[u] * a.xrs);
+                else xv[u] = xj[(int64_t)m.c[u] * a.xrs];
             } else {
                 xv[u] = T(0);
             }
@@ -409,24 +418,31 @@ __device__ __forceinline__ bool row_exec_rp(const SolveArgs<T> &a, const RowRegs
         if constexpr (MODE == 1) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (ok && m.c[u] >= 0 && is_sentinel(xv[u])) ok = poll_wait(xj + m.c[u], xv[u], a, waits);
+                if (ok && m.c[u] >= 0 && is_sentinel(xv[u]))
+                    ok = poll_wait(xj + (int64_t)m.c[u] * a.xrs, xv[u], a, waits);
         }
         T acc = bj * m.dinv;
+        // the group shares the row's entries, so `cnt` is uniform: FP64 instructions
+        // (whole-warp pipe cost) are issued for the row's entries only
+        const int cnt = m.end - m.beg;
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc -= m.v[u] * xv[u];
+        for (int u = 0; u < U; ++u) {
+            if (u >= cnt) break;
+            acc -= m.v[u] * xv[u];
+        }
         for (int q = m.beg + U; ok && q < m.end; ++q) {
             const int c = __ldg(a.col + q);
             T xc;
             if constexpr (MODE == 2) xc = xs[(c & (win - 1)) + j * win];
             else if constexpr (MODE == 1) {
-                xc = ld_poll(xj + c);
-                if (is_sentinel(xc)) ok = poll_wait(xj + c, xc, a, waits);
-            } else xc = xj[c];
+                xc = ld_poll(xj + (int64_t)c * a.xrs);
+                if (is_sentinel(xc)) ok = poll_wait(xj + (int64_t)c * a.xrs, xc, a, waits);
+            } else xc = xj[(int64_t)c * a.xrs];
             acc -= __ldg(a.val + q) * xc;
         }
         if (!ok) break;
         const T y = acc;
-        T *dst = a.x + m.orow + (int64_t)j * a.ldx;
+        T *dst = a.x + (int64_t)m.orow * a.xrs + (int64_t)j * a.ldx;
         if constexpr (MODE == 1) st_pub(dst, publishable(y));
         else *dst = y;
         if constexpr (MODE == 2) xs[(m.orow & (win - 1)) + j * win] = y;
@@ -1406,6 +1422,50 @@ __global__ void __launch_bounds__(512, 1) k_blocks(SolveArgs<T> a) {
 // start of sweep t >= 1 the kernel stops the refinement if the last correction
 // was small: max |d_{t-1}| <= dtol * max |x_t|.
 // ----------------------------------------------------------------------------
+// ----------------------------------------------------------------------------
+// Layout change of a block of right-hand sides between the caller's
+// column-major n x R (leading dimension ld) and an internal row-major copy
+// (R consecutive values per row): with one row's R values in one or two cache
+// lines, a right-hand-side tile gathers each parent in one coalesced load
+// instead of R separate sectors.  32 x 32 tiles through shared memory keep
+// both sides coalesced.  k_to_rows also fills `fill` (row-major, n x R) with
+// the all-ones NaN of not-yet-computed values.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_to_rows(const T *__restrict__ src, int64_t ld, T *__restrict__ dst,
+                                                 T *__restrict__ fill, int n, int R) {
+    __shared__ T tile[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {          // column c0 + k, rows r0 + threadIdx.x
+        const int r = r0 + threadIdx.x, c = c0 + k;
+        if (r < n && c < R) tile[k][threadIdx.x] = src[(int64_t)c * ld + r];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {          // row r0 + k, columns c0 + threadIdx.x
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < n && c < R) {
+            dst[(int64_t)r * R + c] = tile[threadIdx.x][k];
+            if (fill) fill[(int64_t)r * R + c] = all_ones<T>();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_to_cols(const T *__restrict__ src, T *__restrict__ dst, int64_t ld, int n,
+                                                 int R) {
+    __shared__ T tile[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {          // row r0 + k, columns c0 + threadIdx.x
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < n && c < R) tile[k][threadIdx.x] = src[(int64_t)r * R + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {          // column c0 + k, rows r0 + threadIdx.x
+        const int r = r0 + threadIdx.x, c = c0 + k;
+        if (r < n && c < R) dst[(int64_t)c * ld + r] = tile[threadIdx.x][k];
+    }
+}
+
 struct ResidualArgs {
     int32_t n, nrhs, sweep;
     const int32_t *__restrict__ rp;
@@ -1416,57 +1476,39 @@ struct ResidualArgs {
     const float *__restrict__ dlo;
     const int32_t *__restrict__ perm;
     const double *b;
-    int64_t ldb;
+    int64_t ldb, b_rs;               // column and row strides of b
     const double *x;
-    int64_t ldx;
-    float *r32;                      // n x nrhs, leading dimension n
+    int64_t ldx, x_rs;               // column and row strides of x
+    float *r32;                      // n x nrhs: element (row, j) at r32[row * r_rs + j * r_cs]
+    int64_t r_rs, r_cs;
     Ctl *ctl;
     double dtol;
 };
 
-static __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
-    __shared__ double s_r[8], s_b[8];
-    if (a.sweep > 0) {
-        const volatile Ctl *c = a.ctl;
-        if (c->done || c->status) return;
-        const double d = bits_to_d(c->dmax[a.sweep - 1]);
-        const double x = bits_to_d(c->xmax[a.sweep - 1]);
-        if (d <= a.dtol * x) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                a.ctl->done = 1;
-                a.ctl->conv = 1;
-            }
-            return;
+// Convergence bookkeeping at the start of a residual pass: true if the
+// refinement already converged (the correction test of the previous sweep).
+__device__ __forceinline__ bool residual_skip(const ResidualArgs &a) {
+    if (a.sweep == 0) return false;
+    const volatile Ctl *c = a.ctl;
+    if (c->done || c->status) return true;
+    const double d = bits_to_d(c->dmax[a.sweep - 1]);
+    const double x = bits_to_d(c->xmax[a.sweep - 1]);
+    if (d <= a.dtol * x) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.ctl->done = 1;
+            a.ctl->conv = 1;
         }
+        return true;
     }
-    double rm = 0.0, bm = 0.0;
-    const int stride = gridDim.x * blockDim.x;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += stride) {
-        const int o = __ldg(a.perm + r);
-        const int beg = __ldg(a.rp + r), end = __ldg(a.rp + r + 1);
-        const double dh = __ldg(a.dhi + r), dl = __ldg(a.dlo + r);
-        for (int j = 0; j < a.nrhs; ++j) {
-            double s = a.b[o + (int64_t)j * a.ldb];
-            bm = fmax(bm, fabs(s));
-            if (a.sweep > 0) {
-                const double *xj = a.x + (int64_t)j * a.ldx;
-                for (int q = beg; q < end; ++q) {
-                    const double xv = xj[__ldg(a.col + q)];
-                    s = fma(-double(__ldg(a.hi + q)), xv, s);
-                    s = fma(-double(__ldg(a.lo + q)), xv, s);
-                }
-                const double xo = xj[o];
-                s = fma(-dh, xo, s);
-                s = fma(-dl, xo, s);
-            }
-            a.r32[o + (int64_t)j * a.n] = float(s);
-            rm = fmax(rm, fabs(s));
-        }
-    }
+    return false;
+}
+
+__device__ __forceinline__ void residual_flush(const ResidualArgs &a, double rm, double bm) {
+    __shared__ double s_r[32], s_b[32];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, off));
-        bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, off));
+        rm = max_abs_bits(rm, __shfl_xor_sync(0xffffffffu, rm, off));
+        bm = max_abs_bits(bm, __shfl_xor_sync(0xffffffffu, bm, off));
     }
     if ((threadIdx.x & 31) == 0) {
         s_r[threadIdx.x >> 5] = rm;
@@ -1475,12 +1517,63 @@ static __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 1; i < int(blockDim.x >> 5); ++i) {
-            rm = fmax(rm, s_r[i]);
-            bm = fmax(bm, s_b[i]);
+            rm = max_abs_bits(rm, s_r[i]);
+            bm = max_abs_bits(bm, s_b[i]);
         }
         atomicMax(&a.ctl->rmax[a.sweep], (unsigned long long)__double_as_longlong(rm));
         if (a.sweep == 0) atomicMax(&a.ctl->bmax, (unsigned long long)__double_as_longlong(bm));
     }
+}
+
+// Thread per row.  Short rows with several right-hand sides form the row's
+// values hi + lo once in FP64 and keep them for all right-hand sides (one FP64
+// FMA per entry and right-hand side instead of two).
+static __global__ void __launch_bounds__(256) k_residual(ResidualArgs a) {
+    if (residual_skip(a)) return;
+    double rm = 0.0, bm = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    constexpr int kRes = 8;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += stride) {
+        const int o = __ldg(a.perm + r);
+        const int beg = __ldg(a.rp + r), end = __ldg(a.rp + r + 1);
+        const double dh = __ldg(a.dhi + r), dl = __ldg(a.dlo + r);
+        const bool short_row = a.nrhs > 1 && end - beg <= kRes;
+        int c8[kRes];
+        double v8[kRes];
+        if (short_row && a.sweep > 0) {
+#pragma unroll
+            for (int u = 0; u < kRes; ++u) {
+                const int q = beg + u;
+                c8[u] = q < end ? __ldg(a.col + q) : 0;
+                v8[u] = q < end ? double(__ldg(a.hi + q)) + double(__ldg(a.lo + q)) : 0.0;
+            }
+        }
+        for (int j = 0; j < a.nrhs; ++j) {
+            double s = a.b[(int64_t)o * a.b_rs + (int64_t)j * a.ldb];
+            bm = max_abs_bits(bm, s);
+            if (a.sweep > 0) {
+                const double *xj = a.x + (int64_t)j * a.ldx;
+                if (short_row) {
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u)
+                        if (beg + u < end) s = fma(-v8[u], xj[(int64_t)c8[u] * a.x_rs], s);
+                    s = fma(-(dh + dl), xj[(int64_t)o * a.x_rs], s);
+                } else {
+                    for (int q = beg; q < end; ++q) {
+                        const double xv = xj[(int64_t)__ldg(a.col + q) * a.x_rs];
+                        s = fma(-double(__ldg(a.hi + q)), xv, s);
+                        s = fma(-double(__ldg(a.lo + q)), xv, s);
+                    }
+                    const double xo = xj[(int64_t)o * a.x_rs];
+                    s = fma(-dh, xo, s);
+                    s = fma(-dl, xo, s);
+                }
+            }
+            a.r32[(int64_t)o * a.r_rs + (int64_t)j * a.r_cs] = float(s);
+            rm = max_abs_bits(rm, s);
+        }
+    }
+    residual_flush(a, rm, bm);
 }
 
 }  // namespace sptrsv

@@ -83,6 +83,7 @@ struct sptrsv_plan {
     int32_t device = -1;
     int32_t num_sms = 0;
     int64_t nnz_off = 0;
+    int32_t max_row_off = 0;      // most off-diagonal entries in one row
     int64_t device_bytes = 0;
     double analyze_ms = 0.0;
     double lnorm = 0.0;           // ||L||inf in FP64 (backward-error test of the refinement)
