@@ -634,7 +634,8 @@ def run_serve(args):
     nnz_solved = float(sum(factors[int(f)].nnz * int(r) for f, r in zip(fid[:submitted], nrhs[:submitted])))
     line = {"metric": "served solves/s (p50/p99 latency)", "value": st["solves_per_s"], "unit": "solves/s",
             "n_gpus": world, "steps": submitted, "warmup": len(plans), "ms_per_step": 1e3 / max(st["solves_per_s"], 1e-9),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refine",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if (args.precision or "f32_refine") == "f64" else "f32+f64-refine",
             "data": "synthetic (seeded generators, Poisson arrivals)",
             "config": {"workload": "serve_10k", "requests": submitted, "rate_per_s": 2000, "factors": len(plans),
                        "sum_n": int(sum(A.n for A in factors)), "hbm_budget_gb": 40, "streams": 32,
