@@ -869,8 +869,9 @@ __device__ __forceinline__ bool row_exec_polled(const SolveArgs<T> &a, const Row
 // warps advance together (warp-uniform loop, per-group publication); right-hand-
 // side tiles run one row per group.
 // ----------------------------------------------------------------------------
+// FP32 right-hand-side tiles of short rows fit 64 registers: two blocks of 512 per SM.
 template <typename T, int LANES, int U, bool RP, bool PRE = false>
-__global__ void __launch_bounds__(512, 1) k_flags(SolveArgs<T> a) {
+__global__ void __launch_bounds__(512, (RP && U <= 4 && sizeof(T) == 4) ? 2 : 1) k_flags(SolveArgs<T> a) {
     constexpr int RPW = 32 / LANES;
     const int lane32 = threadIdx.x & 31;
     const int grp = lane32 / LANES, lane = lane32 % LANES;
