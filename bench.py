@@ -592,6 +592,9 @@ def run_serve(args):
     """10,000 Poisson requests (2,000/s) against 64 resident factors (n log-uniform in
     [10k, 2M], mixed kinds), 1-16 RHS each, FP32 sweeps + FP64 refinement, 40 GB budget;
     compared with the plain FP64 per-request path (one launch per request, one stream)."""
+    # the server's 32 streams need as many hardware queues (the default is 8), or a
+    # long launch blocks the launches queued behind it; read at CUDA context creation
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     import paper_2503_05408_gb300 as sp

@@ -271,10 +271,15 @@ int sptrsv_batch_solve(sptrsv_plan *const *plans, int32_t count, const void *con
 /* --------------------------------------------------------------- serving */
 /* Continuous batching over resident factors.  A dispatcher thread admits
  * submitted requests in arrival order as soon as their device workspace fits
- * the HBM budget left by the registered factors, packs all admitted requests
- * into one launch of the batched executor on a free stream slot and keeps
- * admitting while earlier launches run, so requests that arrive while others
- * are on the GPU overlap with them.  Each request's result does not depend on
+ * the HBM budget left by the registered factors, packs admitted requests into
+ * one launch of the batched executor on a free stream slot and keeps admitting
+ * while earlier launches run, so requests that arrive while others are on the
+ * GPU overlap with them.  A launch lasts as long as its longest request, so one
+ * launch takes requests of one duration class (their factor's wavefront count
+ * in decades: < 1e3, < 1e4, longer), oldest class first.  Slots are CUDA
+ * streams: give the process at least as many hardware queues
+ * (CUDA_DEVICE_MAX_CONNECTIONS, default 8, up to 32, read when the CUDA context
+ * is created) or launches queue behind each other.  Each request's result does not depend on
  * what it was batched with (it is computed by one thread block alone).
  * SPTRSV_SERVE_SERIAL_F64 serves the same stream the plain way - one request
  * per FP64 sptrsv_solve launch, one stream, arrival order - as a baseline with

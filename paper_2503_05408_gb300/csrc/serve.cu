@@ -168,8 +168,15 @@ void finish_request(sptrsv_server *S, uint64_t id, const sptrsv_report &rep, dou
     --S->inflight;
 }
 
-// Continuous mode: harvest finished slots, then fill free slots with every
-// admissible pending request.
+// Continuous mode: harvest finished slots, then fill free slots with admissible
+// pending requests, one duration class per launch.
+// Duration class of a request: its factor's critical path (wavefronts) in
+// decades, 0: < 1000, 1: < 10000, 2: longer.
+int duration_class(const sptrsv_server *S, uint64_t id) {
+    const int32_t lv = S->factors[S->reqs.at(id).fid]->h.nlevels;
+    return lv < 1000 ? 0 : lv < 10000 ? 1 : 2;
+}
+
 bool continuous_step(sptrsv_server *S) {
     bool did = false;
     for (Slot &sl : S->slots) {
@@ -199,8 +206,17 @@ bool continuous_step(sptrsv_server *S) {
         int cnt = 0;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            while (!S->pending.empty() && cnt < S->opts.max_batch) {
-                const uint64_t id = S->pending.front();
+            // A launch lasts as long as its longest item and holds its stream
+            // until then, so a launch takes requests of one duration class only
+            // (the class of the oldest pending request, then its peers in arrival
+            // order): long dependency chains do not hold short requests back.
+            const int cls = S->pending.empty() ? 0 : duration_class(S, S->pending.front());
+            for (auto pit = S->pending.begin(); pit != S->pending.end() && cnt < S->opts.max_batch;) {
+                const uint64_t id = *pit;
+                if (duration_class(S, id) != cls) {
+                    ++pit;
+                    continue;
+                }
                 Request &r = S->reqs[id];
                 const sptrsv_plan *p = S->factors[r.fid];
                 BatchItem &it = sl.h_items[cnt];
@@ -209,7 +225,7 @@ bool continuous_step(sptrsv_server *S) {
                 size_t off = 0;
                 const size_t need = batch_item_workspace(it, S->refine);
                 if (!S->arena.alloc(need, off)) break;             // FIFO: wait for memory
-                S->pending.pop_front();
+                pit = S->pending.erase(pit);
                 r.state = 1;
                 r.ws_off = off;
                 r.ws_bytes = need;
