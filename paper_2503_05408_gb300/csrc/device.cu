@@ -170,7 +170,7 @@ using WalkKern = void (*)(SolveArgs<T>, int, int);
 constexpr int tile_for(int lanes) { return lanes == 1 ? 8 : lanes == 2 ? 4 : lanes == 4 ? 2 : 1; }
 constexpr int kRpTile = 8;
 
-bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 32; }
+bool lanes_ok(int lanes) { return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32; }
 bool rp_ok(int tile) { return tile == 4 || tile == 8 || tile == 16 || tile == 32; }
 
 template <typename T, bool RP>
@@ -200,6 +200,7 @@ Kern<T> flags_kernel(int lanes, bool pre, bool short_rows = false) {
             case 2: return pre ? k_flags<T, 2, tile_for(2), false, true> : k_flags<T, 2, tile_for(2), false>;
             case 4: return pre ? k_flags<T, 4, tile_for(4), false, true> : k_flags<T, 4, tile_for(4), false>;
             case 8: return pre ? k_flags<T, 8, tile_for(8), false, true> : k_flags<T, 8, tile_for(8), false>;
+            case 16: return pre ? k_flags<T, 16, tile_for(16), false, true> : k_flags<T, 16, tile_for(16), false>;
             case 32: return pre ? k_flags<T, 32, tile_for(32), false, true> : k_flags<T, 32, tile_for(32), false>;
             default: return nullptr;
         }
@@ -212,6 +213,7 @@ Kern<T> local_kernel(int lanes, bool pre) {
         case 2: return pre ? k_local<T, 2, tile_for(2), true> : k_local<T, 2, tile_for(2), false>;
         case 4: return pre ? k_local<T, 4, tile_for(4), true> : k_local<T, 4, tile_for(4), false>;
         case 8: return pre ? k_local<T, 8, tile_for(8), true> : k_local<T, 8, tile_for(8), false>;
+        case 16: return pre ? k_local<T, 16, tile_for(16), true> : k_local<T, 16, tile_for(16), false>;
         case 32: return pre ? k_local<T, 32, tile_for(32), true> : k_local<T, 32, tile_for(32), false>;
         default: return nullptr;
     }
@@ -223,6 +225,7 @@ Kern<T> blocks_kernel(int lanes) {
         case 2: return k_blocks<T, 2>;
         case 4: return k_blocks<T, 4>;
         case 8: return k_blocks<T, 8>;
+        case 16: return k_blocks<T, 16>;
         case 32: return k_blocks<T, 32>;
         default: return nullptr;
     }
@@ -243,6 +246,7 @@ WalkKern<T> walk_kernel(int lanes) {
             case 2: return k_walk<T, 2, tile_for(2), GRID, RING, false>;
             case 4: return k_walk<T, 4, tile_for(4), GRID, RING, false>;
             case 8: return k_walk<T, 8, tile_for(8), GRID, RING, false>;
+            case 16: return k_walk<T, 16, tile_for(16), GRID, RING, false>;
             case 32: return k_walk<T, 32, tile_for(32), GRID, RING, false>;
             default: return nullptr;
         }
@@ -530,7 +534,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         c.lanes = tile;
     } else {
         c.lanes = o.lanes ? o.lanes : auto_lanes(p);
-        if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8 or 32");
+        if (!lanes_ok(c.lanes)) return fail(SPTRSV_ERR_ARG, "lanes must be 1, 2, 4, 8, 16 or 32");
     }
     if (o.eager_sum < 0 || o.eager_sum > 2) return fail(SPTRSV_ERR_ARG, "eager_sum must be 0, 1 or 2");
     c.eager = o.eager_sum != SPTRSV_EAGER_OFF;
@@ -937,7 +941,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     const bool small = int64_t(p->h.n) * nrhs <= 400000;
     // row mappings: (rhs_tile, lanes); entry-split lanes, plus right-hand-side tiles for nrhs >= 2
     std::vector<std::pair<int, int>> maps;
-    for (int lanes : {1, 2, 4, 8, 32}) maps.push_back({1, lanes});
+    for (int lanes : {1, 2, 4, 8, 16, 32}) maps.push_back({1, lanes});
     if (nrhs >= 2)
         for (int tile : {4, 8, 16, 32})
             if (tile / 2 < nrhs) maps.push_back({tile, 0});
