@@ -3,21 +3,25 @@
 // The factor is stored in "device order": superstep-contiguous (Sec. 5),
 // and inside a superstep grouped by block (core) and phase (depth among
 // same-block parents).  Column ids stay ORIGINAL row ids, so every gather
-// reads the caller's x (original order) directly and every row writes its
-// result to x[perm[r]]: no un-permute pass and no internal copy of x.
+// reads x in original order directly and every row writes its result to
+// x[perm[r]]: no un-permute pass.
 //
-// Three executors walk the same structure:
-//  * k_grid   persistent grid; a superstep with a single wide phase is spread
-//             over every warp of the grid, a superstep with several blocks
-//             gives each block to one thread block (the paper's core) which
-//             steps through the block's phases with __syncthreads; one
-//             grid-wide barrier separates supersteps (Sec. 2.2 BSP model).
-//  * k_flags  persistent grid without barriers: rows are taken in device
-//             order and every row waits on per-row ready flags of its
-//             parents (the flag holds the solve's epoch, so flags never need
-//             resetting).
-//  * k_cta    one thread block walks all supersteps, phases separated by
-//             __syncthreads (small factors; also the batched executor's unit).
+// The executors:
+//  * k_walk<GRID>  persistent grid; every warp of the grid takes a share of a
+//             superstep's rows, one grid-wide barrier separates supersteps
+//             (Sec. 2.2 BSP model).  k_blocks: a superstep with several blocks
+//             gives each block to one thread block (the paper's core), which
+//             steps through its phases with __syncthreads.
+//  * k_flags  persistent grid without barriers: rows are dealt to warps in
+//             device order and every row polls its parents' values (x starts
+//             as an all-ones NaN; a published value is the ready signal).
+//  * k_local  persistent grid, rows partitioned over the blocks for locality;
+//             parents of the same block are polled in shared memory.
+//  * k_stage / k_walk<CTA>  one thread block walks all supersteps, phases
+//             separated by __syncthreads, the phases staged by bulk copies
+//             (small factors; also the batched executor's unit).
+// Right-hand-side tiles may run on internal row-major copies of b and x
+// (k_to_rows / k_to_cols change the layout at the ends).
 //
 // Every wait is bounded (%globaltimer); on expiry the kernel records
 // SPTRSV_ERR_TIMEOUT in the status word and returns - it never traps.
