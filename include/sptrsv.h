@@ -138,6 +138,23 @@ int sptrsv_plan_stats(const sptrsv_plan *plan, sptrsv_stats *out);
 int sptrsv_plan_export(const sptrsv_plan *plan, int32_t *level, int32_t *sigma, int32_t *pi,
                        int32_t *perm);
 
+/* Host-only: the row -> thread block partition the block-local executor
+ * (SPTRSV_SYNC_LOCAL) builds for `blocks` thread blocks, for inspection and
+ * tests.  Sec. 3's locality goal at SM granularity: in (wavefront, id) order a
+ * row joins the block holding most of its parents of the two previous
+ * wavefronts (weight 4 for the previous one, 1 for the one before) unless that
+ * block took ceil(1.25 * width / blocks) rows of the row's wavefront or holds
+ * row_cap rows; else the block with the fewest rows of the wavefront.
+ *   A            : the factor (validated as in sptrsv_analyze)
+ *   row_cap      : rows one block may hold (0 = unlimited)
+ *   block_of_row : out, n entries, the block of each row
+ *   position     : out, n entries, the row's position in its block's list;
+ *                  every block's list is in (wavefront, id) order
+ * Errors: ARG (sizes, NULL outputs, rows exceeding blocks * row_cap), and the
+ * validation errors of sptrsv_analyze. */
+int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
+                           int32_t *position);
+
 /* Release a plan and its device memory (NULL is a no-op).  The caller must
  * ensure no enqueued solve still uses it. */
 void sptrsv_destroy(sptrsv_plan *plan);

@@ -117,6 +117,7 @@ def lib():
                                               ctypes.POINTER(vp)]),
             "sptrsv_plan_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
             "sptrsv_plan_export": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+            "sptrsv_local_partition": (ctypes.c_int, [ctypes.POINTER(CSRStruct), i32, i32, vp, vp]),
             "sptrsv_destroy": (None, [vp]),
             "sptrsv_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
             "sptrsv_solve": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
@@ -198,6 +199,19 @@ class ScheduleExport:
     sigma: np.ndarray
     pi: np.ndarray
     perm: np.ndarray
+
+
+def local_partition(A, blocks, row_cap=0):
+    """Host-only: (block of each row, position in its block's list) of the block-local
+    executor's partition for ``blocks`` thread blocks (``sptrsv_local_partition``)."""
+    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.col, dtype=np.int32)
+    val = np.ascontiguousarray(A.val, dtype=np.float64)
+    csr = CSRStruct(int(A.n), int(col.size), _ptr(rowptr), _ptr(col), _ptr(val))
+    blk = np.zeros(int(A.n), dtype=np.int32)
+    pos = np.zeros(int(A.n), dtype=np.int32)
+    _check(lib().sptrsv_local_partition(ctypes.byref(csr), int(blocks), int(row_cap), _ptr(blk), _ptr(pos)))
+    return blk, pos
 
 
 class Plan:

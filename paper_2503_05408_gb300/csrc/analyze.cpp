@@ -121,6 +121,78 @@ int32_t ring_window(const sptrsv_csr *A, const HostSchedule &h) {
 
 }  // namespace
 
+// Block-local partition (SPTRSV_SYNC_LOCAL; Sec. 3's locality applied to the
+// thread blocks of a persistent grid).  Rows are taken in (wavefront, id)
+// order.  A row goes to the block holding most of its parents of the two
+// previous wavefronts (weight 4 for the previous wavefront, which holds its
+// last-finishing parent, 1 for the one before), as long as that block has taken
+// fewer than ceil(1.25 * width / nb) rows of the row's wavefront and has room;
+// otherwise to the block with the fewest rows of this wavefront (then the
+// fewest rows overall).  The cap keeps every wavefront spread over all blocks,
+// the vote keeps dependency chains inside a block.  Rows join their block's
+// list in (wavefront, id) order, which the executor's progress argument needs.
+bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                     const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
+                     std::vector<int32_t> &lidx, std::vector<int32_t> &load) {
+    constexpr double kSlack = 1.25;
+    if (nb < 1 || int64_t(row_cap) * nb < int64_t(n)) return false;
+    std::vector<int32_t> lstart(size_t(nlevels) + 1, 0), ord(n);
+    for (int32_t v = 0; v < n; ++v) lstart[level[v] + 1]++;
+    for (int32_t l = 0; l < nlevels; ++l) lstart[l + 1] += lstart[l];
+    {
+        std::vector<int32_t> fill(lstart.begin(), lstart.end() - 1);
+        for (int32_t v = 0; v < n; ++v) ord[fill[level[v]]++] = v;   // (wavefront, id) order
+    }
+    blk.assign(n, -1);
+    lidx.assign(n, 0);
+    load.assign(nb, 0);
+    std::vector<int32_t> cnt(nb, 0);
+    std::vector<std::pair<int32_t, int32_t>> tally;
+    int32_t cur = -1, cap = 0;
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = ord[t], l = level[v];
+        if (l != cur) {
+            cur = l;
+            std::fill(cnt.begin(), cnt.end(), 0);
+            const double w = double(lstart[l + 1] - lstart[l]);
+            cap = std::max<int32_t>(1, int32_t(std::ceil(w * kSlack / nb)));
+        }
+        tally.clear();
+        const int32_t dr = row_of[v];
+        for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q) {
+            const int32_t c = col[q], lc = level[c];
+            if (lc < l - 2) continue;
+            const int32_t w = lc == l - 1 ? 4 : 1, b = blk[c];
+            bool found = false;
+            for (auto &e : tally)
+                if (e.first == b) {
+                    e.second += w;
+                    found = true;
+                    break;
+                }
+            if (!found) tally.push_back({b, w});
+        }
+        int32_t best = -1, bestw = 0;
+        for (const auto &e : tally)
+            if (cnt[e.first] < cap && load[e.first] < row_cap &&
+                (e.second > bestw || (e.second == bestw && cnt[e.first] < cnt[best]))) {
+                best = e.first;
+                bestw = e.second;
+            }
+        if (best < 0) {
+            for (int32_t b = 0; b < nb; ++b)
+                if (load[b] < row_cap &&
+                    (best < 0 || cnt[b] < cnt[best] || (cnt[b] == cnt[best] && load[b] < load[best])))
+                    best = b;
+        }
+        blk[v] = best;
+        lidx[v] = load[best]++;
+        cnt[best]++;
+    }
+    return true;
+}
+
+
 int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h) {
     const int32_t n = A->n;
     h.n = n;
@@ -336,6 +408,34 @@ int sptrsv_plan_export(const sptrsv_plan *p, int32_t *level, int32_t *sigma, int
     if (sigma && bytes) std::memcpy(sigma, p->h.sigma.data(), bytes);
     if (pi && bytes) std::memcpy(pi, p->h.pi.data(), bytes);
     if (perm && bytes) std::memcpy(perm, p->h.perm.data(), bytes);
+    return SPTRSV_OK;
+}
+
+int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
+                           int32_t *position) {
+    clear_error();
+    if (!A || blocks < 1 || row_cap < 0) return fail(SPTRSV_ERR_ARG, "bad arguments");
+    int st = validate_csr(A);
+    if (st) return st;
+    const int32_t n = A->n;
+    if (n > 0 && (!block_of_row || !position)) return fail(SPTRSV_ERR_ARG, "output arrays are NULL");
+    std::vector<int32_t> level;
+    const int32_t nlevels = n ? compute_levels(A, level) : 0;
+    // off-diagonal parents in original order (the diagonal is each row's last entry)
+    std::vector<int32_t> rp(size_t(n) + 1, 0), col, row_of(n);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1] - 1; ++q) col.push_back(A->col[q]);
+        rp[i + 1] = int32_t(col.size());
+        row_of[i] = i;
+    }
+    std::vector<int32_t> blk, lidx, load;
+    if (!local_partition(n, blocks, row_cap ? row_cap : std::max<int32_t>(n, 1), level, nlevels, rp.data(),
+                         col.data(), row_of.data(), blk, lidx, load))
+        return fail(SPTRSV_ERR_ARG, "rows do not fit blocks * row_cap");
+    if (n) {
+        std::memcpy(block_of_row, blk.data(), size_t(n) * sizeof(int32_t));
+        std::memcpy(position, lidx.data(), size_t(n) * sizeof(int32_t));
+    }
     return SPTRSV_OK;
 }
 

@@ -341,16 +341,6 @@ const void *kernel_ptr(const LaunchCfg &c) {
 }
 
 // ------------------------------------------------------------------ block-local layout
-// Rows are assigned to nb thread blocks in (wavefront, id) order.  A row goes to
-// the block holding most of its parents of the two previous wavefronts (weight
-// 4 for the previous wavefront, which holds its last-finishing parent, 1 for
-// the one before), as long as that block has taken fewer than
-// ceil(1.25 * width / nb) rows of the row's wavefront; otherwise to the block
-// with the fewest rows of this wavefront (then the fewest rows overall).  The
-// cap keeps every wavefront spread over all blocks, the vote keeps dependency
-// chains inside a block.
-constexpr double kLocalSlack = 1.25;
-
 void free_local(DeviceBuffers &d) {
     void *ptrs[] = {d.l_rp, d.l_col, d.l_perm, d.l_blk_row, d.l_val, d.l_dinv, d.l_s32, d.l_dinv32};
     for (void *q : ptrs)
@@ -385,64 +375,14 @@ int ensure_local(sptrsv_plan *p, int nb) {
     if ((st = download(d.rp, size_t(n) + 1, rp)) || (st = download(d.col, nnz, col))) return st;
     std::vector<int32_t> dev_of(n);
     for (int32_t r = 0; r < n; ++r) dev_of[h.dev_perm[r]] = r;
-    // rows in (wavefront, id) order: counting sort by wavefront
-    std::vector<int32_t> lstart(size_t(h.nlevels) + 1, 0), ord(n);
-    for (int32_t v = 0; v < n; ++v) lstart[h.level[v] + 1]++;
-    for (int32_t l = 0; l < h.nlevels; ++l) lstart[l + 1] += lstart[l];
-    {
-        std::vector<int32_t> fill(lstart.begin(), lstart.end() - 1);
-        for (int32_t v = 0; v < n; ++v) ord[fill[h.level[v]]++] = v;
-    }
     // every block keeps all of its rows' values in shared memory: cap the block size
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     const int32_t row_cap = int32_t((int64_t(optin) - 1024) / ((p->values & SPTRSV_VALUES_F64) ? 8 : 4));
-    if (int64_t(row_cap) * nb < int64_t(n))
+    std::vector<int32_t> blk, lidx, load;
+    if (!local_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk, lidx, load))
         return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the shared "
                                         "memory of " + std::to_string(nb) + " blocks");
-    std::vector<int32_t> blk(n), lidx(n), cnt(nb, 0), load(nb, 0);
-    std::vector<std::pair<int32_t, int32_t>> tally;
-    int32_t cur = -1, cap = 0;
-    for (int32_t t = 0; t < n; ++t) {
-        const int32_t v = ord[t], l = h.level[v];
-        if (l != cur) {
-            cur = l;
-            std::fill(cnt.begin(), cnt.end(), 0);
-            const double w = double(lstart[l + 1] - lstart[l]);
-            cap = std::max<int32_t>(1, int32_t(std::ceil(w * kLocalSlack / nb)));
-        }
-        tally.clear();
-        const int32_t dr = dev_of[v];
-        for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q) {
-            const int32_t c = col[q], lc = h.level[c];
-            if (lc < l - 2) continue;
-            const int32_t w = lc == l - 1 ? 4 : 1, b = blk[c];
-            bool found = false;
-            for (auto &e : tally)
-                if (e.first == b) {
-                    e.second += w;
-                    found = true;
-                    break;
-                }
-            if (!found) tally.push_back({b, w});
-        }
-        int32_t best = -1, bestw = 0;
-        for (const auto &e : tally)
-            if (cnt[e.first] < cap && load[e.first] < row_cap &&
-                (e.second > bestw || (e.second == bestw && cnt[e.first] < cnt[best]))) {
-                best = e.first;
-                bestw = e.second;
-            }
-        if (best < 0) {
-            for (int32_t b = 0; b < nb; ++b)
-                if (load[b] < row_cap &&
-                    (best < 0 || cnt[b] < cnt[best] || (cnt[b] == cnt[best] && load[b] < load[best])))
-                    best = b;
-        }
-        blk[v] = best;
-        lidx[v] = load[best]++;
-        cnt[best]++;
-    }
     std::vector<int32_t> bstart(size_t(nb) + 1, 0);
     for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
     // column ids in the block-local order: a parent of the same block -> its

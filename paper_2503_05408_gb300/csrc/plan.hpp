@@ -104,6 +104,14 @@ using TunedCfg = sptrsv_plan::TunedCfg;
 namespace sptrsv {
 // analyze.cpp
 int validate_csr(const sptrsv_csr *A);
+// Block-local partition (used by SPTRSV_SYNC_LOCAL).  Rows are taken in
+// (wavefront, id) order; row v's off-diagonal parents are col[rp[row_of[v]] ..
+// rp[row_of[v] + 1]) (original ids).  Outputs: blk[v] in [0, nb), lidx[v] = v's
+// position in its block's (wavefront, id) list, load[b] = rows of block b.
+// Returns false if the rows do not fit nb blocks of row_cap rows.
+bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                     const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
+                     std::vector<int32_t> &lidx, std::vector<int32_t> &load);
 int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h);
 // growlocal.cpp
 int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,

@@ -150,3 +150,57 @@ def test_stats_on_configs(L):
     p = _host_plan(A)
     st = p.stats()
     assert st["levels"] == 478 and st["n"] == 4_096_000 and st["nnz"] == 16_307_200
+
+
+# ------------------------------------------------------------ block-local partition
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("blocks", [1, 3, 152])
+def test_local_partition_invariants(L, name, blocks):
+    """The executor's progress argument needs every block's list in (wavefront, id)
+    order; balance needs at most ceil(1.25 * width / blocks) rows of a wavefront per block."""
+    A = CASES[name]()
+    blk, pos = sp.local_partition(A, blocks)
+    lv, nlev = oracle.levels(A)
+    lv = np.asarray(lv)
+    assert blk.min() >= 0 and blk.max() < blocks
+    width = np.bincount(lv, minlength=nlev)
+    for b in range(blocks):
+        rows = np.nonzero(blk == b)[0]
+        if rows.size == 0:
+            continue
+        order = rows[np.argsort(pos[rows])]
+        assert np.array_equal(np.sort(pos[rows]), np.arange(rows.size))          # positions 0..k-1
+        key = lv[order].astype(np.int64) * A.n + order                              # (wavefront, id)
+        assert np.all(np.diff(key) > 0)
+        per_level = np.bincount(lv[rows], minlength=nlev)
+        cap = np.maximum(1, np.ceil(width * 1.25 / blocks))
+        assert np.all(per_level <= cap)
+
+
+def test_local_partition_keeps_chains_in_one_block(L):
+    # a bidiagonal factor is one dependency chain: every row follows its parent
+    n = 200
+    A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)])
+    blk, pos = sp.local_partition(A, 8)
+    assert np.all(blk == blk[0]) and np.array_equal(pos, np.arange(n))
+
+
+def test_local_partition_row_cap(L):
+    A = W.laplace2d_lower(4096, 64)
+    blk, pos = sp.local_partition(A, 4, row_cap=1024)
+    assert np.bincount(blk, minlength=4).max() <= 1024
+    with pytest.raises(sp.SptrsvError) as e:
+        sp.local_partition(A, 4, row_cap=1000)          # 4 * 1000 < 4096 rows
+    assert e.value.status == sp.ERR_ARG
+
+
+def test_local_partition_locality_on_random_window(L):
+    # most edges to a previous-wavefront parent stay inside a block (the executor's purpose)
+    A = W.random_window_lower(60_000, 6, 20000, 0)
+    blk, pos = sp.local_partition(A, 152)
+    lv = np.asarray(oracle.levels(A)[0])
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    off = A.col != rows
+    r, c = rows[off], A.col[off]
+    prev = lv[c] == lv[r] - 1
+    assert np.mean(blk[r][prev] == blk[c][prev]) > 0.5
