@@ -9,6 +9,12 @@ The oracle and the library share no code: only the seeded input generators in
 What it computes (each function cites the passage it follows):
 
 * ``solve``          forward substitution, Eq. 2.1, sequential FP64 (C)
+* ``solve_upper``    backward substitution for upper-triangular U (diagonal first
+  in each row), the other direction of the method (C)
+* ``solve_transposed``  L^T x = b from L's rows, column-oriented backward
+  substitution (C)
+* ``levels_upper``   wavefronts of an upper factor's DAG (row i waits on its
+  columns j > i), plain reverse pass
 * ``spmv``           y = A x in FP64 (C), for residual checks
 * ``levels``         wavefronts of the DAG of Sec. 2.2 / Fig. 1.1 (C)
 * ``growlocal``      the GrowLocal scheduler, Sec. 3 / Algorithm 3.1 (C)
@@ -65,6 +71,11 @@ def _load():
             lib.oracle_solve_fp64.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _f64p,
                                               _f64p, ctypes.c_int64, _f64p, ctypes.c_int64]
             lib.oracle_solve_fp64.restype = None
+            for name in ("oracle_solve_upper_fp64", "oracle_solve_lower_transposed_fp64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _f64p,
+                               _f64p, ctypes.c_int64, _f64p, ctypes.c_int64]
+                fn.restype = None
             lib.oracle_spmv_fp64.argtypes = [ctypes.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
             lib.oracle_spmv_fp64.restype = None
             lib.oracle_levels.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
@@ -121,6 +132,58 @@ def solve(A, b: np.ndarray) -> np.ndarray:
     lib.oracle_solve_fp64(A.n, b2.shape[1], _p(rp, _i32p), _p(c, _i32p), _p(v, _f64p),
                           _p(b2, _f64p), A.n, _p(x, _f64p), A.n)
     return x.reshape(np.shape(b)) if np.ndim(b) == 1 else x
+
+
+def validate_upper(U) -> None:
+    """Upper-triangular CSR: strictly increasing columns, the non-zero diagonal
+    present and stored first in every row."""
+    n = U.n
+    rp, c, v = _arrays(U)
+    if rp.size != n + 1 or rp[0] != 0 or np.any(np.diff(rp) < 1) or rp[-1] != c.size:
+        raise InvalidFactor("bad row pointers (every row needs at least its diagonal)")
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    if np.any(c < rows) or np.any(c >= n):
+        raise InvalidFactor("entry below the diagonal or out of range")
+    same_row = rows[1:] == rows[:-1]
+    if np.any(same_row & (c[1:] <= c[:-1])):
+        raise InvalidFactor("columns not strictly increasing within a row")
+    first = rp[:-1]
+    if np.any(c[first] != np.arange(n)):
+        raise InvalidFactor("diagonal missing")
+    if np.any(v[first] == 0.0):
+        raise InvalidFactor("zero diagonal")
+
+
+def _solve_with(fn, A, b):
+    lib = _load()
+    rp, c, v = _arrays(A)
+    b2 = np.asfortranarray(np.asarray(b, dtype=np.float64).reshape(A.n, -1))
+    x = np.empty_like(b2, order="F")
+    getattr(lib, fn)(A.n, b2.shape[1], _p(rp, _i32p), _p(c, _i32p), _p(v, _f64p),
+                     _p(b2, _f64p), A.n, _p(x, _f64p), A.n)
+    return x.reshape(np.shape(b)) if np.ndim(b) == 1 else x
+
+
+def solve_upper(U, b: np.ndarray) -> np.ndarray:
+    """Backward substitution U x = b in FP64 (U upper-triangular, diagonal first)."""
+    return _solve_with("oracle_solve_upper_fp64", U, b)
+
+
+def solve_transposed(L, b: np.ndarray) -> np.ndarray:
+    """L^T x = b in FP64 from L's rows (L lower-triangular, diagonal last)."""
+    return _solve_with("oracle_solve_lower_transposed_fp64", L, b)
+
+
+def levels_upper(U):
+    """Wavefronts of an upper factor: row i waits on the rows j > i it references,
+    so one pass from the last row: level(i) = 1 + max level over those j (0 if none)."""
+    rp, c, _ = _arrays(U)
+    lv = np.zeros(U.n, dtype=np.int32)
+    for i in range(U.n - 1, -1, -1):
+        js = c[rp[i] + 1:rp[i + 1]]
+        if js.size:
+            lv[i] = lv[js].max() + 1
+    return lv, int(lv.max()) + 1 if U.n else 0
 
 
 def spmv(A, x: np.ndarray) -> np.ndarray:

@@ -8,6 +8,10 @@
  *
  * Everything here is deliberately plain and sequential:
  *   - oracle_solve_fp64     forward substitution, Eq. 2.1, row by row in FP64
+ *   - oracle_solve_upper_fp64           backward substitution (the upper-
+ *                           triangular counterpart of Eq. 2.1), row by row
+ *   - oracle_solve_lower_transposed_fp64  L^T x = b from L's rows, column-
+ *                           oriented backward substitution
  *   - oracle_spmv_fp64      y = A x in FP64 (used for residual checks in tests)
  *   - oracle_levels         wavefronts of the DAG of Sec. 2.2 (Fig. 1.1)
  *   - oracle_growlocal      the GrowLocal scheduler of Sec. 3 / Algorithm 3.1
@@ -41,6 +45,47 @@ void oracle_solve_fp64(int32_t n, int32_t nrhs, const int32_t *rowptr, const int
             for (int32_t p = rowptr[i]; p < last; ++p)
                 s = s - val[p] * xj[col[p]];
             xj[i] = s / val[last];
+        }
+    }
+}
+
+/* Backward substitution for upper-triangular U (the method's other direction):
+ * x_i = (b_i - sum_{j>i} U_ij x_j) / U_ii for i = n-1 down to 0, the sum in
+ * ascending column order.  Upper CSR convention: columns strictly increasing
+ * within a row, the diagonal present and stored FIRST. */
+void oracle_solve_upper_fp64(int32_t n, int32_t nrhs, const int32_t *rowptr, const int32_t *col,
+                             const double *val, const double *b, int64_t ldb, double *x, int64_t ldx)
+{
+    for (int32_t r = 0; r < nrhs; ++r) {
+        const double *bj = b + (int64_t)r * ldb;
+        double *xj = x + (int64_t)r * ldx;
+        for (int32_t i = n - 1; i >= 0; --i) {
+            double s = bj[i];
+            const int32_t d = rowptr[i];                /* diagonal position */
+            for (int32_t p = d + 1; p < rowptr[i + 1]; ++p)
+                s = s - val[p] * xj[col[p]];
+            xj[i] = s / val[d];
+        }
+    }
+}
+
+/* L^T x = b for lower-triangular L given by its rows (diagonal last): since
+ * (L^T x)_j = sum_k L_kj x_k, take k = n-1 down to 0, finish x_k = x_k / L_kk
+ * and remove L_kj x_k from every x_j of row k (column-oriented backward
+ * substitution; no transpose is formed). */
+void oracle_solve_lower_transposed_fp64(int32_t n, int32_t nrhs, const int32_t *rowptr, const int32_t *col,
+                                        const double *val, const double *b, int64_t ldb, double *x,
+                                        int64_t ldx)
+{
+    for (int32_t r = 0; r < nrhs; ++r) {
+        const double *bj = b + (int64_t)r * ldb;
+        double *xj = x + (int64_t)r * ldx;
+        for (int32_t i = 0; i < n; ++i) xj[i] = bj[i];
+        for (int32_t k = n - 1; k >= 0; --k) {
+            const int32_t last = rowptr[k + 1] - 1;
+            xj[k] = xj[k] / val[last];
+            for (int32_t p = rowptr[k]; p < last; ++p)
+                xj[col[p]] = xj[col[p]] - val[p] * xj[k];
         }
     }
 }

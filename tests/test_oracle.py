@@ -326,3 +326,77 @@ def _csr_from_coo(n, r, c, v):
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.add.at(rowptr, r + 1, 1)
     return np.cumsum(rowptr).astype(np.int32), c.astype(np.int32), v
+
+
+# ------------------------------------------------------ backward substitution (upper / L^T)
+def _dense(A):
+    D = np.zeros((A.n, A.n))
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    D[rows, A.col] = A.val
+    return D
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (7, 2), (33, 3), (64, 4)])
+def test_solve_upper_and_transposed_match_dense_lapack(n, seed):
+    rng = np.random.default_rng(100 + seed)
+    D = np.tril(rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.4), -1)
+    D += np.diag(rng.uniform(1.0, 3.0, n) * np.where(rng.random(n) < 0.5, -1, 1))
+    rows, cols = np.nonzero(D)
+    L = W.from_pattern(n, list(zip(rows.tolist(), cols.tolist())))
+    L.val[:] = D[np.repeat(np.arange(n), np.diff(L.rowptr)), L.col]
+    U = W.transpose(L)
+    oracle.validate_upper(U)
+    assert np.array_equal(_dense(U), D.T)
+    B = rng.standard_normal((n, 3))
+    Xref = scipy.linalg.solve_triangular(D.T, B, lower=False)
+    assert oracle.rel_error(oracle.solve_upper(U, B), Xref) < 1e-12
+    assert oracle.rel_error(oracle.solve_transposed(L, B), Xref) < 1e-12
+
+
+def test_solve_upper_bidiagonal_closed_form():
+    # diag 2, super-diagonal -1, b = 1: x_i = (1 + x_{i+1}) / 2 = 1 - 2^-(n-i), exact in FP64.
+    n = 80
+    U = W.transpose(W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0))
+    want = 1.0 - 2.0 ** -(n - np.arange(n, dtype=np.float64))
+    assert np.array_equal(oracle.solve_upper(U, np.ones(n)), want)
+    L = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
+    assert np.array_equal(oracle.solve_transposed(L, np.ones(n)), want)
+    lv, nl = oracle.levels_upper(U)
+    assert nl == n and lv[0] == n - 1 and lv[-1] == 0
+
+
+def test_solve_upper_diagonal_closed_form():
+    rng = np.random.default_rng(6)
+    n = 40
+    d = rng.uniform(0.5, 2.0, n)
+    L = W.from_pattern(n, [])
+    L.val[:] = d
+    b = rng.standard_normal(n)
+    assert np.array_equal(oracle.solve_upper(W.transpose(L), b), b / d)
+    assert np.array_equal(oracle.solve_transposed(L, b), b / d)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.laplace2d_lower(4096, 64),
+    lambda: W.random_window_lower(30000, 6, 20000, 0),
+])
+def test_upper_manufactured_solution_and_levels(make):
+    L = make()
+    U = W.transpose(L)
+    xs, b = W.manufactured_rhs(U, 2, seed=8)
+    x = oracle.solve_upper(U, b)
+    assert oracle.rel_error(x, xs) < 1e-13
+    assert oracle.rel_error(oracle.solve_transposed(L, b), xs) < 1e-13
+    # the upper DAG is the lower one reversed: same number of wavefronts
+    assert oracle.levels_upper(U)[1] == oracle.levels(L)[1]
+
+
+def test_validate_upper_rejects_bad_inputs():
+    U = W.transpose(W.laplace2d_lower(64, 8))
+    oracle.validate_upper(U)
+    bad = W.CSR(U.n, U.rowptr.copy(), U.col.copy(), U.val.copy())
+    bad.val[bad.rowptr[5]] = 0.0
+    with pytest.raises(oracle.InvalidFactor):
+        oracle.validate_upper(bad)
+    with pytest.raises(oracle.InvalidFactor):
+        oracle.validate_upper(W.laplace2d_lower(64, 8))       # lower, diagonal last

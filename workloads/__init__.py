@@ -44,7 +44,7 @@ __all__ = [
 
 @dataclass
 class CSR:
-    """Square lower-triangular CSR factor (int32 indices, float64 values)."""
+    """Square triangular CSR factor (int32 indices, float64 values); lower unless built by ``transpose``."""
     n: int
     rowptr: np.ndarray
     col: np.ndarray
@@ -230,6 +230,19 @@ def from_pattern(n: int, entries, diag: float = 1.0, off: float = -1.0) -> CSR:
     counts = [len(set(x)) for x in rows]
     offcols = np.array([c for x in rows for c in sorted(set(x))], dtype=np.int32)
     return _assemble(n, counts, offcols, np.full(offcols.size, off), np.full(n, diag), "pattern")
+
+
+def transpose(A: CSR) -> CSR:
+    """A^T in CSR (columns sorted): the transpose of a lower factor is an upper
+    factor whose rows start with the diagonal."""
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.rowptr))
+    order = np.lexsort((rows, A.col))                   # by column, then row
+    col_t = rows[order].astype(np.int32)
+    val_t = np.asarray(A.val)[order]
+    counts = np.bincount(A.col, minlength=A.n)
+    rp_t = np.zeros(A.n + 1, dtype=np.int32)
+    rp_t[1:] = np.cumsum(counts)
+    return CSR(A.n, rp_t, col_t, val_t, name=(A.name + "^T") if A.name else "", meta=dict(A.meta))
 
 
 def manufactured_rhs(A: CSR, nrhs: int = 1, seed: int = 0, dtype=np.float64):
