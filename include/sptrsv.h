@@ -97,7 +97,20 @@ typedef struct {
     int32_t values;    /* SPTRSV_VALUES_* mask; 0 = F64 | F32                              */
     int32_t device;    /* CUDA device ordinal, or -1: analyse on the host only (no upload;
                           sptrsv_solve then returns SPTRSV_ERR_NO_DEVICE)                  */
+    int32_t triangle;  /* SPTRSV_TRI_*: which system the plan solves (default LOWER)      */
 } sptrsv_analyze_opts;
+
+/* The system a plan solves.  The method covers both substitution directions
+ * (Sec. 2, Eq. 2.1 and its backward counterpart): an upper factor's DAG is the
+ * lower one reversed, so UPPER and LOWER_TRANSPOSED are analysed as the lower
+ * factor L' with rows and columns numbered backwards (row i of the system is
+ * row n-1-i of L') and solved by the same kernels; b, x and sptrsv_plan_export
+ * stay in the caller's numbering.
+ *   LOWER            : L x = b, CSR of L, diagonal last in every row
+ *   UPPER            : U x = b, CSR of U, columns increasing, diagonal FIRST
+ *   LOWER_TRANSPOSED : L^T x = b from the CSR of L (diagonal last), e.g. the
+ *                      second half of an incomplete-Cholesky preconditioner   */
+enum { SPTRSV_TRI_LOWER = 0, SPTRSV_TRI_UPPER = 1, SPTRSV_TRI_LOWER_TRANSPOSED = 2 };
 
 /* Fill `o` with the defaults above (LEVELS, k = 0, 20, 1.5, 500, 0.97, both value
  * copies, device 0). */

@@ -23,6 +23,8 @@ ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT = -5, -6, -7, -8, -9
 ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE = -10, -11, -12
 
 SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
+TRI_LOWER, TRI_UPPER, TRI_LOWER_TRANSPOSED = 0, 1, 2
+_TRI = {"lower": TRI_LOWER, "upper": TRI_UPPER, "lower_transposed": TRI_LOWER_TRANSPOSED}
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
 SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL = 0, 1, 2, 3, 4, 5
@@ -50,7 +52,7 @@ class CSRStruct(ctypes.Structure):
 class AnalyzeOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("growth", ctypes.c_double), ("L", ctypes.c_double), ("accept", ctypes.c_double),
-                ("values", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("values", ctypes.c_int32), ("device", ctypes.c_int32), ("triangle", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -215,10 +217,12 @@ def local_partition(A, blocks, row_cap=0):
 
 
 class Plan:
-    """An analysed factor: ``Plan(A)`` with ``A`` having ``n, rowptr, col, val`` (numpy)."""
+    """An analysed factor: ``Plan(A)`` with ``A`` having ``n, rowptr, col, val`` (numpy).
+    ``triangle``: "lower" (L x = b), "upper" (U x = b, diagonal first in each row) or
+    "lower_transposed" (L^T x = b from L's rows)."""
 
     def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
-                 values=VALUES_F64 | VALUES_F32, device=0):
+                 values=VALUES_F64 | VALUES_F32, device=0, triangle="lower"):
         lb = lib()
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         self._col = np.ascontiguousarray(A.col, dtype=np.int32)
@@ -232,6 +236,7 @@ class Plan:
         o.mode = _MODE[mode] if isinstance(mode, str) else int(mode)
         o.k, o.alpha0, o.growth, o.L, o.accept = int(k), alpha0, growth, L, accept
         o.values, o.device = int(values), int(device)
+        o.triangle = _TRI[triangle] if isinstance(triangle, str) else int(triangle)
         h = ctypes.c_void_p()
         self.handle = None
         _check(lb.sptrsv_analyze(ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))

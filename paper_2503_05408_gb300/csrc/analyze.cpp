@@ -119,6 +119,69 @@ int32_t ring_window(const sptrsv_csr *A, const HostSchedule &h) {
     return 0;
 }
 
+// Upper-triangular input: columns strictly increasing, diagonal present, first
+// and non-zero.  Mirrors validate_csr's rules for the other direction.
+int validate_upper_csr(const sptrsv_csr *A) {
+    if (!A || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->rowptr || !A->col || !A->val)))
+        return fail(SPTRSV_ERR_ARG, "bad csr");
+    if (A->nnz > INT32_MAX) return fail(SPTRSV_ERR_ARG, "nnz exceeds int32 indexing");
+    if (A->n == 0) return SPTRSV_OK;
+    const int32_t n = A->n;
+    if (A->rowptr[0] != 0 || A->rowptr[n] != A->nnz) return fail(SPTRSV_ERR_ARG, "bad row pointers");
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t b = A->rowptr[i], e = A->rowptr[i + 1];
+        if (e <= b || e > A->nnz) return fail(SPTRSV_ERR_ARG, "bad row pointers");
+        if (A->col[b] != i) return fail(SPTRSV_ERR_ZERO_DIAG, "row " + std::to_string(i) + ": diagonal not first");
+        if (A->val[b] == 0.0) return fail(SPTRSV_ERR_ZERO_DIAG, "row " + std::to_string(i) + ": zero diagonal");
+        for (int32_t q = b + 1; q < e; ++q) {
+            if (A->col[q] >= n) return fail(SPTRSV_ERR_ARG, "column out of range");
+            if (A->col[q] <= A->col[q - 1])
+                return fail(A->col[q] < i ? SPTRSV_ERR_NOT_LOWER : SPTRSV_ERR_UNSORTED_OR_DUP,
+                            "row " + std::to_string(i) + ": entry below the diagonal, unsorted or duplicate");
+        }
+    }
+    return SPTRSV_OK;
+}
+
+// L' with ids i' = n-1-i from an upper factor U: row i' lists U's row i
+// backwards, so its columns n-1-j increase and the diagonal comes last.
+void reverse_upper(const sptrsv_csr *U, std::vector<int32_t> &rp, std::vector<int32_t> &col,
+                   std::vector<double> &val) {
+    const int32_t n = U->n;
+    rp.assign(size_t(n) + 1, 0);
+    col.resize(size_t(U->nnz));
+    val.resize(size_t(U->nnz));
+    int64_t o = 0;
+    for (int32_t ip = 0; ip < n; ++ip) {
+        const int32_t i = n - 1 - ip;
+        for (int32_t q = U->rowptr[i + 1] - 1; q >= U->rowptr[i]; --q, ++o) {
+            col[size_t(o)] = n - 1 - U->col[q];
+            val[size_t(o)] = U->val[q];
+        }
+        rp[size_t(ip) + 1] = int32_t(o);
+    }
+}
+
+// L' with ids i' = n-1-i for L^T, from the rows of L: entry (k, j) of L is
+// entry (j, k) of L^T, i.e. (n-1-j, n-1-k) of L'.  Rows of L taken from the last
+// one append every L' row's columns in increasing order, the diagonal last.
+void reverse_transpose(const sptrsv_csr *L, std::vector<int32_t> &rp, std::vector<int32_t> &col,
+                       std::vector<double> &val) {
+    const int32_t n = L->n;
+    rp.assign(size_t(n) + 1, 0);
+    for (int64_t q = 0; q < L->nnz; ++q) rp[size_t(n - 1 - L->col[q]) + 1]++;
+    for (int32_t i = 0; i < n; ++i) rp[size_t(i) + 1] += rp[size_t(i)];
+    std::vector<int32_t> fill(rp.begin(), rp.end() - 1);
+    col.resize(size_t(L->nnz));
+    val.resize(size_t(L->nnz));
+    for (int32_t k = n - 1; k >= 0; --k)
+        for (int32_t q = L->rowptr[k]; q < L->rowptr[k + 1]; ++q) {
+            const int32_t r = n - 1 - L->col[q];
+            col[size_t(fill[r])] = n - 1 - k;
+            val[size_t(fill[r]++)] = L->val[q];
+        }
+}
+
 }  // namespace
 
 // Block-local partition (SPTRSV_SYNC_LOCAL; Sec. 3's locality applied to the
@@ -325,6 +388,7 @@ void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o) {
     o->accept = 0.97;
     o->values = SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32;
     o->device = 0;
+    o->triangle = SPTRSV_TRI_LOWER;
 }
 
 int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out) {
@@ -342,7 +406,29 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
             return fail(SPTRSV_ERR_ARG, "GrowLocal needs alpha0 >= 1, growth > 1, L >= 0, accept > 0");
     }
     const auto t0 = std::chrono::steady_clock::now();
-    int st = validate_csr(csr);
+    // UPPER and LOWER_TRANSPOSED: analyse the lower factor L' numbered backwards
+    std::vector<int32_t> rrp, rcol;
+    std::vector<double> rval;
+    sptrsv_csr lowered;
+    int st;
+    if (o.triangle == SPTRSV_TRI_UPPER) {
+        if ((st = validate_upper_csr(csr))) return st;
+        reverse_upper(csr, rrp, rcol, rval);
+    } else if (o.triangle == SPTRSV_TRI_LOWER_TRANSPOSED) {
+        if ((st = validate_csr(csr))) return st;
+        reverse_transpose(csr, rrp, rcol, rval);
+    } else if (o.triangle != SPTRSV_TRI_LOWER) {
+        return fail(SPTRSV_ERR_ARG, "unknown triangle");
+    }
+    if (o.triangle != SPTRSV_TRI_LOWER) {
+        lowered.n = csr->n;
+        lowered.nnz = csr->nnz;
+        lowered.rowptr = rrp.data();
+        lowered.col = rcol.data();
+        lowered.val = rval.data();
+        csr = &lowered;
+    }
+    st = validate_csr(csr);
     if (st) return st;
     int32_t sms = 1;
     if (o.device >= 0) {
@@ -365,6 +451,7 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     }
     p->values = o.values;
     p->device = o.device;
+    p->reversed = o.triangle != SPTRSV_TRI_LOWER;
     for (int32_t i = 0; i < csr->n; ++i) {
         double rs = 0.0;
         for (int32_t q = csr->rowptr[i]; q < csr->rowptr[i + 1]; ++q) rs += std::abs(csr->val[q]);
@@ -403,11 +490,22 @@ int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
 
 int sptrsv_plan_export(const sptrsv_plan *p, int32_t *level, int32_t *sigma, int32_t *pi, int32_t *perm) {
     if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
-    const size_t bytes = size_t(p->h.n) * sizeof(int32_t);
-    if (level && bytes) std::memcpy(level, p->h.level.data(), bytes);
-    if (sigma && bytes) std::memcpy(sigma, p->h.sigma.data(), bytes);
-    if (pi && bytes) std::memcpy(pi, p->h.pi.data(), bytes);
-    if (perm && bytes) std::memcpy(perm, p->h.perm.data(), bytes);
+    const int32_t n = p->h.n;
+    const size_t bytes = size_t(n) * sizeof(int32_t);
+    if (!p->reversed) {
+        if (level && bytes) std::memcpy(level, p->h.level.data(), bytes);
+        if (sigma && bytes) std::memcpy(sigma, p->h.sigma.data(), bytes);
+        if (pi && bytes) std::memcpy(pi, p->h.pi.data(), bytes);
+        if (perm && bytes) std::memcpy(perm, p->h.perm.data(), bytes);
+        return SPTRSV_OK;
+    }
+    // reversed plans: row i of the caller's system is row n-1-i of L'
+    for (int32_t i = 0; i < n; ++i) {
+        if (level) level[i] = p->h.level[size_t(n - 1 - i)];
+        if (sigma) sigma[i] = p->h.sigma[size_t(n - 1 - i)];
+        if (pi) pi[i] = p->h.pi[size_t(n - 1 - i)];
+        if (perm) perm[i] = n - 1 - p->h.perm[size_t(i)];
+    }
     return SPTRSV_OK;
 }
 

@@ -76,7 +76,8 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
         const int32_t v = h.dev_perm[r];
         const int32_t lo = A->rowptr[v], last = A->rowptr[v + 1] - 1;
         for (int32_t q = lo; q < last; ++q) {
-            col.push_back(A->col[q]);
+            // reversed plans: the kernels address b and x in the caller's numbering
+            col.push_back(p->reversed ? n - 1 - A->col[q] : A->col[q]);
             val.push_back(A->val[q]);
         }
         diag[r] = A->val[last];
@@ -120,7 +121,12 @@ int upload_plan(sptrsv_plan *p, const sptrsv_csr *A) {
         if ((st = upload(dinv32, &d.dinv32, &bytes))) return st;
         if ((st = upload(s32, &d.s32, &bytes))) return st;
     }
-    if ((st = upload(h.dev_perm, &d.perm, &bytes))) return st;
+    {
+        std::vector<int32_t> perm(h.dev_perm);
+        if (p->reversed)
+            for (auto &v : perm) v = n - 1 - v;
+        if ((st = upload(perm, &d.perm, &bytes))) return st;
+    }
     if ((st = upload(h.step_blk, &d.step_blk, &bytes))) return st;
     if ((st = upload(h.blk_phase, &d.blk_phase, &bytes))) return st;
     if ((st = upload(h.phase_row, &d.phase_row, &bytes))) return st;
@@ -373,6 +379,8 @@ int ensure_local(sptrsv_plan *p, int nb) {
     // the device-order factor back from the device (the caller's CSR is not kept)
     std::vector<int32_t> rp, col;
     if ((st = download(d.rp, size_t(n) + 1, rp)) || (st = download(d.col, nnz, col))) return st;
+    if (p->reversed)                                   // back to the analysed factor's numbering
+        for (auto &c : col) c = n - 1 - c;
     std::vector<int32_t> dev_of(n);
     for (int32_t r = 0; r < n; ++r) dev_of[h.dev_perm[r]] = r;
     // every block keeps all of its rows' values in shared memory: cap the block size
@@ -396,14 +404,17 @@ int ensure_local(sptrsv_plan *p, int nb) {
         int32_t o = lrp[t];
         for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q, ++o) {
             const int32_t c = col[q];
-            lcol[o] = blk[c] == blk[v] ? -(lidx[c] + 2) : c;
+            lcol[o] = blk[c] == blk[v] ? -(lidx[c] + 2) : (p->reversed ? n - 1 - c : c);
             src[o] = q;
         }
         lrp[t + 1] = o;
     }
     int64_t bytes = 0;
+    std::vector<int32_t> lperm_out(lperm);
+    if (p->reversed)
+        for (auto &v : lperm_out) v = n - 1 - v;
     if ((st = upload(lrp, &d.l_rp, &bytes)) || (st = upload(lcol, &d.l_col, &bytes)) ||
-        (st = upload(lperm, &d.l_perm, &bytes)) || (st = upload(bstart, &d.l_blk_row, &bytes)))
+        (st = upload(lperm_out, &d.l_perm, &bytes)) || (st = upload(bstart, &d.l_blk_row, &bytes)))
         return st;
     // values: a gather of the device-order arrays into the block-local order
     auto regather = [&](auto *dval, auto *ddiag, auto **lval, auto **ldiag) -> int {

@@ -81,6 +81,7 @@ struct sptrsv_plan {
     sptrsv::HostSchedule h;
     int32_t values = 0;
     int32_t device = -1;
+    bool reversed = false;        // UPPER / LOWER_TRANSPOSED: analysed as L' with ids i' = n-1-i
     int32_t num_sms = 0;
     int64_t nnz_off = 0;
     int32_t max_row_off = 0;      // most off-diagonal entries in one row

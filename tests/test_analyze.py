@@ -204,3 +204,33 @@ def test_local_partition_locality_on_random_window(L):
     r, c = rows[off], A.col[off]
     prev = lv[c] == lv[r] - 1
     assert np.mean(blk[r][prev] == blk[c][prev]) > 0.5
+
+
+# ------------------------------------------------------------ upper and transposed systems
+@pytest.mark.parametrize("name", ["lap2d_64", "lap3d_20", "random_50k", "banded_30k", "er_20k", "fig1_1"])
+def test_upper_and_transposed_levels_bit_exact(L, name):
+    Lo = CASES[name]()
+    U = W.transpose(Lo)
+    lv, nlev = oracle.levels_upper(U)
+    for A, tri in ((U, "upper"), (Lo, "lower_transposed")):
+        p = sp.Plan(A, device=-1, triangle=tri)
+        ex = p.export()
+        assert np.array_equal(ex.level, lv)
+        assert p.stats()["levels"] == nlev
+        # wavefront schedule: sigma = level, and the permutation lists rows by (sigma, id)
+        # in the reversed numbering, i.e. by (level, descending id) here
+        assert np.array_equal(ex.sigma, lv)
+        key = ex.level[ex.perm].astype(np.int64) * A.n + (A.n - 1 - ex.perm)
+        assert np.all(np.diff(key) > 0) and np.array_equal(np.sort(ex.perm), np.arange(A.n))
+
+
+def test_upper_validation_errors(L):
+    U = W.transpose(W.laplace2d_lower(64, 8))
+    bad = W.CSR(U.n, U.rowptr.copy(), U.col.copy(), U.val.copy())
+    bad.val[bad.rowptr[7]] = 0.0
+    with pytest.raises(sp.SptrsvError) as e:
+        sp.Plan(bad, device=-1, triangle="upper")
+    assert e.value.status == sp.ERR_ZERO_DIAG
+    with pytest.raises(sp.SptrsvError) as e:
+        sp.Plan(W.laplace2d_lower(64, 8), device=-1, triangle="upper")   # a lower factor
+    assert e.value.status in (sp.ERR_ZERO_DIAG, sp.ERR_NOT_LOWER)

@@ -89,3 +89,30 @@ def test_batch_full_config_256x8(precision):
     (bs, xs, reps), = run_batch(factors, [8] * 256, precision=precision)
     worst = max(oracle.rel_error(x, oracle.solve(A, b)) for A, b, x in zip(factors, bs, xs))
     assert worst <= F64_TOL
+
+
+def test_batch_mixes_lower_and_upper_plans():
+    # a batch may hold plans of both directions; each item matches its own oracle
+    import oracle as O
+    facs = [W.batch_factor(f) for f in range(6)]
+    plans, bs, xs_, refs = [], [], [], []
+    for i, A in enumerate(facs):
+        if i % 2:
+            U = W.transpose(A)
+            p = sp.Plan(U, triangle="upper")
+            _, b = W.manufactured_rhs(U, 3, seed=400 + i)
+            ref = O.solve_upper(U, b)
+        else:
+            p = sp.Plan(A)
+            _, b = W.manufactured_rhs(A, 3, seed=400 + i)
+            ref = O.solve(A, b)
+        plans.append(p)
+        bd = torch.from_numpy(np.ascontiguousarray(b.T)).cuda().T
+        bs.append(bd)
+        xs_.append(torch.empty_strided(bd.shape, bd.stride(), dtype=bd.dtype, device=bd.device))
+        refs.append(ref)
+    batch = sp.Batch(plans, [3] * len(plans), precision="f64")
+    batch.run(bs, xs_)
+    torch.cuda.synchronize()
+    for x, ref in zip(xs_, refs):
+        assert O.rel_error(x.cpu().numpy(), ref) <= 1e-12

@@ -301,3 +301,59 @@ def test_staged_walker_matches_register_walker():
             x1, r1 = solve_gpu(plan, b, sync="cta", rhs_tile=tile)
             x2, r2 = solve_gpu(plan, b, sync="cta_regs", rhs_tile=tile)
             assert np.max(np.abs(x1 - x2)) <= 1e-14 * np.max(np.abs(x2))
+
+
+# ------------------------------------------------------------ upper and transposed systems
+UPPER_CASES = ["lap2d_64x64", "lap3d_24", "random_60k", "banded_20k", "er_30k", "dense_rows"]
+
+
+@pytest.mark.parametrize("name", UPPER_CASES)
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local"])
+@pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
+def test_upper_and_transposed_parity(name, sync, tri):
+    Lo = SMALL[name]()
+    U = W.transpose(Lo)
+    xs, b = W.manufactured_rhs(U, 1, seed=31)
+    xo = oracle.solve_upper(U, b)
+    plan = sp.Plan(U if tri == "upper" else Lo, triangle=tri)
+    x, rep = solve_gpu(plan, b, sync=sync)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
+@pytest.mark.parametrize("nrhs,rhs_tile", [(5, 0), (5, 1), (32, 32)])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta"])
+def test_upper_multi_rhs(tri, nrhs, rhs_tile, sync):
+    Lo = W.laplace3d_lower(20 ** 3, 20)
+    U = W.transpose(Lo)
+    xs, b = W.manufactured_rhs(U, nrhs, seed=32)
+    plan = sp.Plan(U if tri == "upper" else Lo, triangle=tri)
+    x, rep = solve_gpu(plan, b, sync=sync, rhs_tile=rhs_tile)
+    assert oracle.rel_error(x, oracle.solve_transposed(Lo, b)) <= F64_TOL
+
+
+@pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "local"])
+def test_upper_refine_and_growlocal(tri, sync):
+    Lo = W.make_dominant(W.erdos_renyi_lower(30_000, 3e-4, 2))
+    U = W.transpose(Lo)
+    xs, b = W.manufactured_rhs(U, 1, seed=33)
+    xo = oracle.solve_upper(U, b)
+    A = U if tri == "upper" else Lo
+    x, rep = solve_gpu(sp.Plan(A, triangle=tri), b, sync=sync, precision="f32_refine")
+    assert oracle.rel_error(x, xo) <= F64_TOL and rep["berr"] <= 1e-13
+    x, rep = solve_gpu(sp.Plan(A, mode="growlocal", k=16, triangle=tri), b, sync=sync)
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+def test_upper_full_size_3d():
+    Lo = W.laplace3d_lower(160 ** 3, 160)
+    U = W.transpose(Lo)
+    xs, b = W.manufactured_rhs(U, 1, seed=34)
+    xo = oracle.solve_upper(U, b)
+    assert oracle.rel_error(xo, xs) < 1e-13
+    plan = sp.Plan(U, triangle="upper")
+    for sync in ("flags", "local"):
+        x, rep = solve_gpu(plan, b, sync=sync)
+        assert oracle.rel_error(x, xo) <= F64_TOL
