@@ -59,8 +59,18 @@ WORKLOADS = {
                                       "32 RHS column-major"),
     "lap3d_160_f64_r32": dict(make=lambda: W.config_3d_160(nrhs=32), dtype="f64", nrhs=32,
                               desc="7-point Laplacian 160^3, FP64, 32 RHS column-major"),
+    "random_1m_upper_f64": dict(make=lambda: _upper(W.config_random_1m()), dtype="f64", nrhs=1, triangle="upper",
+                                desc="U = L^T of the 1M random factor (backward substitution), FP64, 1 RHS"),
 }
 SPECIAL = ("batch_256x8", "serve_10k")
+
+
+def _upper(cfg):
+    """The transpose of a lower configuration, with a right-hand side for it."""
+    L, _, _ = cfg
+    U = W.transpose(L)
+    xs, b = W.manufactured_rhs(U, 1, seed=11)
+    return U, xs, b
 
 
 def parse_args():
@@ -200,15 +210,22 @@ def algorithmic_bytes(n, nnz, nrhs, val_bytes, idx_bytes=4, x_bytes=None):
 
 
 # ------------------------------------------------------------------ CPU baseline
-def cpu_oracle_leg(A, b, seconds: float, max_solves: int | None = None):
+def oracle_solver(spec):
+    """The oracle's sequential FP64 substitution for the workload's direction."""
+    import oracle
+    return oracle.solve_upper if spec.get("triangle", "lower") == "upper" else oracle.solve
+
+
+def cpu_oracle_leg(A, b, seconds: float, max_solves: int | None = None, solver=None):
     """Time the CPU oracle (1 host core, sequential FP64) on whole solves of the factor."""
     import oracle
-    x = oracle.solve(A, b)                       # warm (page-in, compile)
+    solver = solver or oracle.solve
+    x = solver(A, b)                             # warm (page-in, compile)
     times = []
     t_end = time.perf_counter() + seconds
     while True:
         t0 = time.perf_counter()
-        x = oracle.solve(A, b)
+        x = solver(A, b)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() > t_end or (max_solves and len(times) >= max_solves):
             break
@@ -225,15 +242,15 @@ def run_reference(args):
         return 0
     spec = WORKLOADS[args.workload]
     A, xs, b = spec["make"]()
-    import oracle
-    oracle.solve(A, b)
+    solver = oracle_solver(spec)
+    solver(A, b)
     times = []
     for _ in range(args.warmup):
-        oracle.solve(A, b)
+        solver(A, b)
     budget_end = time.perf_counter() + 120.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.solve(A, b)
+        solver(A, b)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() > budget_end:
             break
@@ -269,7 +286,7 @@ def run_ours(args):
     A, xs, b_np = spec["make"]()
     nrhs = spec["nrhs"]
     t0 = time.perf_counter()
-    plan = sp.Plan(A, mode="levels", device=local)
+    plan = sp.Plan(A, mode="levels", device=local, triangle=spec.get("triangle", "lower"))
     analyze_s = time.perf_counter() - t0
     st = plan.stats()
 
@@ -382,7 +399,8 @@ def run_ours(args):
         line["roofline"]["achieved"] = bytes_launch * rep["sweeps"] / mean_s / 1e9
         line["roofline"]["frac"] = line["roofline"]["achieved"] / peak
     if rank == 0 and not args.no_cpu_baseline:
-        cpu, x_or, cpu_s = cpu_oracle_leg(A, b_np, args.cpu_seconds, max_solves=None if nrhs == 1 else 3)
+        cpu, x_or, cpu_s = cpu_oracle_leg(A, b_np, args.cpu_seconds, max_solves=None if nrhs == 1 else 3,
+                                          solver=oracle_solver(spec))
         line["cpu_baseline"] = cpu
         import oracle
         line["err_vs_oracle"] = oracle.rel_error(x.double().cpu().numpy().reshape(A.n, -1), x_or)
