@@ -138,7 +138,7 @@ def profile_traffic(kernel_tag: str):
             if ":" in line:
                 k, _, v = line.partition(":")
                 fields[k.strip()] = v.strip()
-    if fields.get("source_sha1") != kernel_source_sha1():
+    if (fields.get("source_sha1", "").split() or [""])[0] != kernel_source_sha1():
         return None
     try:
         return float(fields["traffic_bytes_per_launch"])
@@ -146,13 +146,17 @@ def profile_traffic(kernel_tag: str):
         return None
 
 
+# The single-solve kernels and their launch and layout code: a profile's
+# counters stay valid while neither file changes.
+KERNEL_SOURCES = ("kernels.cuh", "device.cu")
+
+
 def kernel_source_sha1():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2503_05408_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 
