@@ -18,6 +18,8 @@ What it computes (each function cites the passage it follows):
 * ``spmv``           y = A x in FP64 (C), for residual checks
 * ``levels``         wavefronts of the DAG of Sec. 2.2 / Fig. 1.1 (C)
 * ``growlocal``      the GrowLocal scheduler, Sec. 3 / Algorithm 3.1 (C)
+* ``growlocal_blocks``  block-parallel scheduling, Sec. 3.1: GrowLocal on each
+  diagonal block's sub-DAG (full-row weights), block schedules concatenated
 * ``level_schedule`` sigma = wavefront, pi = 0 (the wavefront scheduler, Sec. 1)
 * ``check_schedule`` Definition 2.1 plus the bookkeeping rules of a schedule
 * ``permutation``    the reordering of Sec. 5: sort by (superstep, core, id)
@@ -28,8 +30,10 @@ What it computes (each function cites the passage it follows):
 Pins (tests/test_oracle.py): the Fig. 1.1 worked example, dense triangular
 solves on tiny inputs, closed forms for diagonal and bidiagonal factors,
 closed-form wavefront counts of natural-order stencils, manufactured
-solutions, the hand-derived GrowLocal example on a diagonal matrix and brute
-force Definition 2.1 checks on small random DAGs.
+solutions, the hand-derived GrowLocal example on a diagonal matrix, a
+hand-derived two-block schedule that only the full-row weights produce, the
+closed form of one block per row, and brute force Definition 2.1 checks on
+small random DAGs.
 """
 from __future__ import annotations
 
@@ -48,6 +52,7 @@ _lock = threading.Lock()
 _lib = None
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
 _f64p = ctypes.POINTER(ctypes.c_double)
 
 
@@ -84,6 +89,10 @@ def _load():
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _i32p, _i32p]
             lib.oracle_growlocal.restype = ctypes.c_int32
+            lib.oracle_growlocal_weighted.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, ctypes.c_int32,
+                                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                      ctypes.c_double, _i32p, _i32p]
+            lib.oracle_growlocal_weighted.restype = ctypes.c_int32
             _lib = lib
     return _lib
 
@@ -236,6 +245,53 @@ def growlocal(A, k: int, alpha0: float = 20.0, growth: float = 1.5, L: float = 5
     if S < 0:
         raise MemoryError("oracle_growlocal failed")
     return sigma, pi, int(S)
+
+
+def growlocal_blocks(A, k: int, blocks: int, alpha0: float = 20.0, growth: float = 1.5,
+                     L: float = 500.0, accept: float = 0.97):
+    """Block-parallel scheduling (Sec. 3.1, Fig. 3.2), run one block after another.
+
+    The rows are cut into ``blocks`` diagonal blocks, block b holding rows
+    floor(b n / blocks) .. floor((b+1) n / blocks) - 1 (the figure's equal
+    blocks).  Each block is scheduled by GrowLocal on its own sub-DAG: its rows,
+    renumbered from 0, keep only the entries in the block's own columns (the
+    edges from earlier blocks are met because those blocks run first), while
+    every vertex keeps the weight of its full row.  The block schedules are
+    concatenated: a vertex of block b gets its superstep plus the number of
+    supersteps of blocks 0..b-1.  Returns (sigma, pi, supersteps)."""
+    if blocks <= 1:
+        return growlocal(A, k, alpha0, growth, L, accept)
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    lib = _load()
+    rp, c, _ = _arrays(A)
+    n = A.n
+    sigma = np.empty(n, dtype=np.int32)
+    pi = np.empty(n, dtype=np.int32)
+    offset = 0
+    for b in range(blocks):
+        r0, r1 = b * n // blocks, (b + 1) * n // blocks
+        m = r1 - r0
+        if m == 0:
+            continue
+        rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp[r0:r1 + 1]))
+        cols = c[rp[r0]:rp[r1]]
+        keep = cols >= r0                       # entries inside the diagonal block
+        sub_rp = np.zeros(m + 1, dtype=np.int32)
+        sub_rp[1:] = np.cumsum(np.bincount(rows[keep], minlength=m))
+        sub_col = np.ascontiguousarray(cols[keep] - r0, dtype=np.int32)
+        weight = np.ascontiguousarray(np.diff(rp[r0:r1 + 1]), dtype=np.int64)   # full rows
+        s_b = np.empty(m, dtype=np.int32)
+        p_b = np.empty(m, dtype=np.int32)
+        S = lib.oracle_growlocal_weighted(m, _p(sub_rp, _i32p), _p(sub_col, _i32p), _p(weight, _i64p),
+                                          int(k), float(alpha0), float(growth), float(L), float(accept),
+                                          _p(s_b, _i32p), _p(p_b, _i32p))
+        if S < 0:
+            raise MemoryError("oracle_growlocal_weighted failed")
+        sigma[r0:r1] = s_b + offset
+        pi[r0:r1] = p_b
+        offset += int(S)
+    return sigma, pi, offset
 
 
 def edges(A):

@@ -15,6 +15,8 @@
  *   - oracle_spmv_fp64      y = A x in FP64 (used for residual checks in tests)
  *   - oracle_levels         wavefronts of the DAG of Sec. 2.2 (Fig. 1.1)
  *   - oracle_growlocal      the GrowLocal scheduler of Sec. 3 / Algorithm 3.1
+ *   - oracle_growlocal_weighted  the same with explicit vertex weights (used by
+ *                           the block-parallel scheduling of Sec. 3.1)
  *
  * Compile with -O2 -ffp-contract=off (no fused multiply-add contraction) so
  * the FP64 results are reproducible on x86 and Arm.
@@ -280,9 +282,24 @@ static void run_attempt(attempt_t *A, int64_t limit)
  *    kept), or right after a worthy attempt in which core 0 took fewer than
  *    floor(alpha) vertices: it ran out of candidates, so every larger alpha
  *    would repeat the same attempt. */
+int32_t oracle_growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                  const int64_t *weight, int32_t k, double alpha0, double growth,
+                                  double L, double accept, int32_t *sigma, int32_t *pi);
+
 int32_t oracle_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
                          double alpha0, double growth, double L, double accept,
                          int32_t *sigma, int32_t *pi)
+{
+    return oracle_growlocal_weighted(n, rowptr, col, NULL, k, alpha0, growth, L, accept, sigma, pi);
+}
+
+/* As oracle_growlocal, with the vertex weights omega(v) given explicitly
+ * (weight == NULL: the row's stored entries).  The block-parallel scheduler of
+ * Sec. 3.1 runs GrowLocal on a diagonal block whose rows lost their entries in
+ * earlier blocks' columns, yet weighs each vertex by its full row. */
+int32_t oracle_growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col,
+                                  const int64_t *weight, int32_t k, double alpha0, double growth,
+                                  double L, double accept, int32_t *sigma, int32_t *pi)
 {
     if (n <= 0)
         return 0;
@@ -291,7 +308,7 @@ int32_t oracle_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, i
     int64_t *w = (int64_t *)malloc((size_t)n * sizeof(int64_t));
     int32_t *missing = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     for (int32_t i = 0; i < n; ++i) {
-        w[i] = rowptr[i + 1] - rowptr[i];
+        w[i] = weight ? weight[i] : (int64_t)(rowptr[i + 1] - rowptr[i]);
         missing[i] = 0;
         for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
             if (col[p] != i) {

@@ -296,6 +296,91 @@ def test_growlocal_every_vertex_once_on_er_100k():
     assert 1 <= S <= nlev
 
 
+# ------------------------------------------------- block-parallel GrowLocal (Sec. 3.1)
+def test_growlocal_blocks_hand_example_full_row_weights():
+    # Rows 0..3: diagonal only (weight 1).  Row 4 <- {0,1,2,3} (weight 5), rows 5..7
+    # diagonal only.  Two blocks {0..3}, {4..7}; k = 2, alpha0 = 1, growth = 2, L = 0.
+    # Block 0 (all ready, weights 1): attempt limit 1: core0 {0}, core1 {1}, beta 2/1;
+    #   limit 2: core0 {0,1}, core1 {2,3}, beta 4/2 (worthy); limit 4: core0 {0..3},
+    #   beta 4/4 < 0.97*2 -> keep {0,1 | 2,3}: one superstep.
+    # Block 1: the edges into row 4 come from block 0 and are dropped, but row 4 keeps
+    #   weight 5.  limit 1: core0 {4} (Omega 5), core1 {5,6,7} (Omega 3), beta 8/5;
+    #   limit 2: core0 {4,5} (6), core1 {6,7} (2), beta 8/6 < 0.97*1.6 -> keep the first.
+    #   (Block-local weights would give core0 {4,5}, core1 {6,7} instead.)
+    # Concatenation: block 1's superstep 0 becomes superstep 1.
+    A = W.from_pattern(8, [(4, 0), (4, 1), (4, 2), (4, 3)])
+    sigma, pi, S = oracle.growlocal_blocks(A, 2, 2, alpha0=1.0, growth=2.0, L=0.0, accept=0.97)
+    assert S == 2
+    assert sigma.tolist() == [0, 0, 0, 0, 1, 1, 1, 1]
+    assert pi.tolist() == [0, 0, 1, 1, 0, 1, 1, 1]
+    assert oracle.check_schedule(A, sigma, pi, 2) == []
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.laplace2d_lower(400, 20),
+    lambda: W.random_window_lower(300, 6, 50, 4),
+])
+def test_growlocal_blocks_one_row_per_block_is_sequential(make):
+    # Every block is one vertex: core 0, superstep 0 of its block -> sigma = id, pi = 0.
+    A = make()
+    sigma, pi, S = oracle.growlocal_blocks(A, 4, A.n)
+    assert S == A.n
+    assert sigma.tolist() == list(range(A.n)) and not pi.any()
+
+
+def _block_diagonal(parts):
+    rp, cols, vals, off = [0], [], [], 0
+    for P in parts:
+        for i in range(P.n):
+            lo, hi = P.rowptr[i], P.rowptr[i + 1]
+            cols += (P.col[lo:hi] + off).tolist()
+            vals += P.val[lo:hi].tolist()
+            rp.append(len(cols))
+        off += P.n
+    return W.CSR(off, np.array(rp, np.int32), np.array(cols, np.int32), np.array(vals), "blockdiag")
+
+
+def test_growlocal_blocks_block_diagonal_matches_separate_schedules():
+    # Three independent parts of 144 rows, cut into the same three blocks: no edge
+    # crosses a block, nothing is dropped and every weight is the block's own, so
+    # each block's schedule is GrowLocal of that part alone, shifted by the
+    # supersteps of the parts before it.
+    parts = [W.laplace2d_lower(144, 12), W.erdos_renyi_lower(144, 0.03, 7),
+             W.random_window_lower(144, 5, 40, 8)]
+    A = _block_diagonal(parts)
+    sigma, pi, S = oracle.growlocal_blocks(A, 3, 3, alpha0=3.0, L=10.0)
+    offset = 0
+    for b, P in enumerate(parts):
+        s_b, p_b, S_b = oracle.growlocal(P, 3, alpha0=3.0, L=10.0)
+        r0 = 144 * b
+        assert np.array_equal(sigma[r0:r0 + 144], s_b + offset)
+        assert np.array_equal(pi[r0:r0 + 144], p_b)
+        offset += S_b
+    assert S == offset
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_growlocal_blocks_valid_and_block_ordered(seed):
+    rng = np.random.default_rng(700 + seed)
+    n = int(rng.integers(1, 500))
+    A = W.erdos_renyi_lower(n, float(rng.uniform(0.002, 0.05)), seed)
+    k = int(rng.integers(1, 7))
+    blocks = int(rng.integers(2, 9))
+    sigma, pi, S = oracle.growlocal_blocks(A, k, blocks, alpha0=float(rng.choice([1.0, 5.0, 20.0])),
+                                           L=float(rng.choice([0.0, 20.0, 500.0])))
+    assert oracle.check_schedule(A, sigma, pi, k) == []
+    # each block owns a contiguous superstep range, in block order, none shared
+    lo = 0
+    for b in range(blocks):
+        r0, r1 = b * n // blocks, (b + 1) * n // blocks
+        if r1 == r0:
+            continue
+        seg = sigma[r0:r1]
+        assert seg.min() == lo
+        lo = int(seg.max()) + 1
+    assert S == lo
+
+
 # ---------------------------------------------------------------- permutation
 @pytest.mark.parametrize("seed", range(5))
 def test_permutation_is_bijection_and_keeps_lower(seed):
