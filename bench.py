@@ -61,8 +61,22 @@ WORKLOADS = {
                               desc="7-point Laplacian 160^3, FP64, 32 RHS column-major"),
     "random_1m_upper_f64": dict(make=lambda: _upper(W.config_random_1m()), dtype="f64", nrhs=1, triangle="upper",
                                 desc="U = L^T of the 1M random factor (backward substitution), FP64, 1 RHS"),
+    "er_100k_f64": dict(make=lambda: _dominant(W.erdos_renyi_lower(100_000, 5e-4, 0)), dtype="f64", nrhs=1,
+                        desc="Erdos-Renyi lower factor n=1e5, p=5e-4 (Sec. 6.2.4 pattern and off-diagonals), "
+                             "diagonal 1+sum|off|, FP64, 1 RHS"),
+    "nb_100k_f64": dict(make=lambda: _dominant(W.narrow_band_lower(100_000, 0.05, 20, 0)), dtype="f64", nrhs=1,
+                        desc="narrow-bandwidth lower factor n=1e5, p=0.05, B=20 (Sec. 6.2.5 pattern and "
+                             "off-diagonals), diagonal 1+sum|off|, FP64, 1 RHS"),
 }
 SPECIAL = ("batch_256x8", "serve_10k")
+
+
+def _dominant(A):
+    """The paper's random pattern with a dominant diagonal (its diagonal scale lets x grow
+    without bound over a hundred wavefronts), and a manufactured right-hand side."""
+    A = W.make_dominant(A)
+    xs, b = W.manufactured_rhs(A, 1, seed=0)
+    return A, xs, b
 
 
 def _upper(cfg):
@@ -89,6 +103,11 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--blocks-per-sm", type=int, default=None)
     ap.add_argument("--rhs-tile", type=int, default=None)
+    ap.add_argument("--schedule", choices=["levels", "growlocal"], default="levels",
+                    help="superstep schedule of the analysis (single-factor workloads)")
+    ap.add_argument("--sched-blocks", type=int, default=0,
+                    help="GrowLocal block-parallel scheduling: diagonal blocks (0/1: whole DAG)")
+    ap.add_argument("--sched-threads", type=int, default=0, help="host threads for the schedule blocks")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="bound of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -290,7 +309,8 @@ def run_ours(args):
     A, xs, b_np = spec["make"]()
     nrhs = spec["nrhs"]
     t0 = time.perf_counter()
-    plan = sp.Plan(A, mode="levels", device=local, triangle=spec.get("triangle", "lower"))
+    plan = sp.Plan(A, mode=args.schedule, device=local, triangle=spec.get("triangle", "lower"),
+                   sched_blocks=args.sched_blocks, sched_threads=args.sched_threads)
     analyze_s = time.perf_counter() - t0
     st = plan.stats()
 
@@ -379,7 +399,8 @@ def run_ours(args):
         "data": "synthetic (seeded generator, see config.description)",
         "config": {"workload": args.workload, "description": spec["desc"], "n": A.n, "nnz": A.nnz,
                    "nrhs": nrhs, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
-                   "levels": st["levels"], "supersteps": st["supersteps"], "schedule": "levels",
+                   "levels": st["levels"], "supersteps": st["supersteps"], "schedule": args.schedule,
+                   "sched_blocks": st["sched_blocks"], "schedule_ms": st["schedule_ms"],
                    "sync": rep["sync_name"], "lanes": rep["lanes"], "grid": rep["grid"],
                    "threads": rep["threads"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -98,6 +98,16 @@ typedef struct {
     int32_t device;    /* CUDA device ordinal, or -1: analyse on the host only (no upload;
                           sptrsv_solve then returns SPTRSV_ERR_NO_DEVICE)                  */
     int32_t triangle;  /* SPTRSV_TRI_*: which system the plan solves (default LOWER)      */
+    int32_t sched_blocks;  /* GROWLOCAL only.  0 or 1: one schedule over the whole DAG.
+                          B > 1: block-parallel scheduling (Sec. 3.1): rows are cut into B
+                          diagonal blocks, block b = rows floor(b n / B) .. floor((b+1) n / B)
+                          - 1; GrowLocal runs on each block's sub-DAG (edges from earlier
+                          blocks dropped, vertex weight = the full row's entry count) and
+                          the block schedules are concatenated: a vertex of block b gets
+                          its block superstep plus the supersteps of blocks 0..b-1.  The
+                          result does not depend on sched_threads.                        */
+    int32_t sched_threads; /* host threads for the blocks; 0 = one per hardware thread,
+                          never more than B                                               */
 } sptrsv_analyze_opts;
 
 /* The system a plan solves.  The method covers both substitution directions
@@ -113,7 +123,7 @@ typedef struct {
 enum { SPTRSV_TRI_LOWER = 0, SPTRSV_TRI_UPPER = 1, SPTRSV_TRI_LOWER_TRANSPOSED = 2 };
 
 /* Fill `o` with the defaults above (LEVELS, k = 0, 20, 1.5, 500, 0.97, both value
- * copies, device 0). */
+ * copies, device 0, LOWER, one schedule block, sched_threads 0). */
 void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o);
 
 typedef struct {
@@ -128,6 +138,9 @@ typedef struct {
     double analyze_ms;       /* host wall time of sptrsv_analyze                           */
     int32_t phases;          /* dependency-free row groups walked by the executors          */
     int32_t ring_rows;       /* shared-memory x ring proven safe for one-block walks (0: none) */
+    double schedule_ms;      /* host wall time of the superstep schedule alone (part of
+                                analyze_ms): wavefronts for LEVELS, GrowLocal otherwise   */
+    int32_t sched_blocks;    /* diagonal blocks the schedule was built on (1: whole DAG)    */
 } sptrsv_stats;
 
 /* Analyse a factor (Sec. 2.2 DAG, Sec. 1 wavefronts, Sec. 3 schedule, Sec. 5

@@ -52,14 +52,16 @@ class CSRStruct(ctypes.Structure):
 class AnalyzeOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("growth", ctypes.c_double), ("L", ctypes.c_double), ("accept", ctypes.c_double),
-                ("values", ctypes.c_int32), ("device", ctypes.c_int32), ("triangle", ctypes.c_int32)]
+                ("values", ctypes.c_int32), ("device", ctypes.c_int32), ("triangle", ctypes.c_int32),
+                ("sched_blocks", ctypes.c_int32), ("sched_threads", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("supersteps", ctypes.c_int32), ("k", ctypes.c_int32), ("max_level_rows", ctypes.c_int32),
                 ("avg_wavefront", ctypes.c_double), ("device_bytes", ctypes.c_int64),
-                ("analyze_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("ring_rows", ctypes.c_int32)]
+                ("analyze_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("ring_rows", ctypes.c_int32),
+                ("schedule_ms", ctypes.c_double), ("sched_blocks", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -219,10 +221,13 @@ def local_partition(A, blocks, row_cap=0):
 class Plan:
     """An analysed factor: ``Plan(A)`` with ``A`` having ``n, rowptr, col, val`` (numpy).
     ``triangle``: "lower" (L x = b), "upper" (U x = b, diagonal first in each row) or
-    "lower_transposed" (L^T x = b from L's rows)."""
+    "lower_transposed" (L^T x = b from L's rows).
+    ``sched_blocks`` > 1 (GrowLocal only): block-parallel scheduling (Sec. 3.1) on
+    ``sched_threads`` host threads (0: one per hardware thread)."""
 
     def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
-                 values=VALUES_F64 | VALUES_F32, device=0, triangle="lower"):
+                 values=VALUES_F64 | VALUES_F32, device=0, triangle="lower", sched_blocks=0,
+                 sched_threads=0):
         lb = lib()
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         self._col = np.ascontiguousarray(A.col, dtype=np.int32)
@@ -237,6 +242,7 @@ class Plan:
         o.k, o.alpha0, o.growth, o.L, o.accept = int(k), alpha0, growth, L, accept
         o.values, o.device = int(values), int(device)
         o.triangle = _TRI[triangle] if isinstance(triangle, str) else int(triangle)
+        o.sched_blocks, o.sched_threads = int(sched_blocks), int(sched_threads)
         h = ctypes.c_void_p()
         self.handle = None
         _check(lb.sptrsv_analyze(ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))

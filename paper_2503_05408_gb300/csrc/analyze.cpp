@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <string>
 #include <thread>
@@ -261,6 +262,7 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
     h.n = n;
     h.nnz = A->nnz;
     h.mode = o.mode;
+    const auto t0 = std::chrono::steady_clock::now();
     h.nlevels = n ? compute_levels(A, h.level) : 0;
     {
         std::vector<int32_t> width(size_t(h.nlevels), 0);
@@ -269,14 +271,19 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
     }
     h.sigma.assign(n, 0);
     h.pi.assign(n, 0);
+    h.sched_blocks = 1;
     if (o.mode == SPTRSV_SCHED_LEVELS) {
         h.k = 1;
         h.sigma = h.level;
         h.S = h.nlevels;
+        h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     } else if (o.mode == SPTRSV_SCHED_GROWLOCAL) {
         h.k = o.k;
-        h.S = growlocal_schedule(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept,
-                                 h.sigma.data(), h.pi.data());
+        h.sched_blocks = std::max(1, o.sched_blocks);
+        const auto t1 = std::chrono::steady_clock::now();
+        h.S = growlocal_blocks(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept, h.sched_blocks,
+                               o.sched_threads, h.sigma.data(), h.pi.data());
+        h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     } else {
         return fail(SPTRSV_ERR_ARG, "unknown schedule mode");
     }
@@ -389,6 +396,8 @@ void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o) {
     o->values = SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32;
     o->device = 0;
     o->triangle = SPTRSV_TRI_LOWER;
+    o->sched_blocks = 0;
+    o->sched_threads = 0;
 }
 
 int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out) {
@@ -405,6 +414,9 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
         if (!(o.alpha0 >= 1.0) || !(o.growth > 1.0) || !(o.L >= 0.0) || !(o.accept > 0.0))
             return fail(SPTRSV_ERR_ARG, "GrowLocal needs alpha0 >= 1, growth > 1, L >= 0, accept > 0");
     }
+    if (o.sched_blocks < 0 || o.sched_threads < 0) return fail(SPTRSV_ERR_ARG, "negative sched_blocks/threads");
+    if (o.sched_blocks > 1 && o.mode != SPTRSV_SCHED_GROWLOCAL)
+        return fail(SPTRSV_ERR_ARG, "sched_blocks > 1 needs the GROWLOCAL schedule");
     const auto t0 = std::chrono::steady_clock::now();
     // UPPER and LOWER_TRANSPOSED: analyse the lower factor L' numbered backwards
     std::vector<int32_t> rrp, rcol;
@@ -444,6 +456,8 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
         st = build_schedule(csr, o, p->h);
     } catch (const std::bad_alloc &) {
         st = fail(SPTRSV_ERR_OOM, "host allocation failed during analysis");
+    } catch (const std::exception &e) {           // e.g. a scheduling thread that could not start
+        st = fail(SPTRSV_ERR_OOM, std::string("analysis failed: ") + e.what());
     }
     if (st) {
         delete p;
@@ -485,6 +499,8 @@ int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
     out->analyze_ms = p->analyze_ms;
     out->phases = int32_t(p->h.phase_row.size()) - 1;
     out->ring_rows = p->h.ring_rows;
+    out->schedule_ms = p->h.schedule_ms;
+    out->sched_blocks = p->h.sched_blocks;
     return SPTRSV_OK;
 }
 

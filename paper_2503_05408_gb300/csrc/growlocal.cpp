@@ -24,11 +24,17 @@
 //  * the superstep keeps the last worthy attempt and ends at the first unworthy
 //    one, or after a worthy attempt in which core 0 got fewer than floor(alpha)
 //    vertices (a larger alpha would repeat that attempt exactly).
+//
+// Block-parallel scheduling (Sec. 3.1, Fig. 3.2): the rows are cut into
+// diagonal blocks, GrowLocal runs on each block's sub-DAG on its own host
+// thread, and the block schedules are concatenated.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <exception>
 #include <functional>
 #include <queue>
+#include <thread>
 #include <vector>
 
 #include "plan.hpp"
@@ -49,23 +55,31 @@ struct Dag {
     std::vector<int32_t> indeg;              // parents of v
 };
 
-Dag make_dag(int32_t n, const int32_t *rowptr, const int32_t *col) {
+// The sub-DAG of rows [r0, r1), numbered from 0.  Parents below r0 belong to
+// earlier blocks, which finish before this block starts, so their edges are
+// dropped; omega(v) stays the entry count of the full row (Sec. 3.1).
+Dag make_dag(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col) {
     Dag g;
+    const int32_t n = r1 - r0;
     g.n = n;
     g.child_ptr.assign(size_t(n) + 1, 0);
     g.weight.resize(n);
-    g.indeg.resize(n);
+    g.indeg.assign(n, 0);
     for (int32_t v = 0; v < n; ++v) {
-        int32_t lo = rowptr[v], hi = rowptr[v + 1];
+        const int32_t lo = rowptr[r0 + v], hi = rowptr[r0 + v + 1];
         g.weight[v] = hi - lo;
-        g.indeg[v] = hi - lo - 1;                 // every stored entry but the diagonal
-        for (int32_t q = lo; q < hi - 1; ++q) g.child_ptr[size_t(col[q]) + 1]++;
+        for (int32_t q = lo; q < hi - 1; ++q)     // every stored entry but the diagonal
+            if (col[q] >= r0) {
+                g.indeg[v]++;
+                g.child_ptr[size_t(col[q] - r0) + 1]++;
+            }
     }
     for (int32_t v = 0; v < n; ++v) g.child_ptr[v + 1] += g.child_ptr[v];
     g.child.resize(g.child_ptr[n]);
     std::vector<int32_t> pos(g.child_ptr.begin(), g.child_ptr.end() - 1);
     for (int32_t v = 0; v < n; ++v)               // ascending v -> children sorted by id
-        for (int32_t q = rowptr[v]; q < rowptr[v + 1] - 1; ++q) g.child[pos[col[q]]++] = v;
+        for (int32_t q = rowptr[r0 + v]; q < rowptr[r0 + v + 1] - 1; ++q)
+            if (col[q] >= r0) g.child[pos[col[q] - r0]++] = v;
     return g;
 }
 
@@ -189,11 +203,14 @@ class Scheduler {
 
 }  // namespace
 
-int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
-                           double alpha0, double growth, double L, double accept,
-                           int32_t *sigma, int32_t *pi) {
-    if (n == 0) return 0;
-    Dag g = make_dag(n, rowptr, col);
+namespace {
+
+// GrowLocal on rows [r0, r1); sigma and pi are indexed by the block-local id.
+int32_t growlocal_range(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col, int32_t k,
+                        double alpha0, double growth, double L, double accept, int32_t *sigma, int32_t *pi) {
+    const int32_t n = r1 - r0;
+    if (n <= 0) return 0;
+    Dag g = make_dag(r0, r1, rowptr, col);
     Scheduler sch(g, k);
     std::vector<char> done(n, 0);
     std::vector<int32_t> keep_v, keep_p;
@@ -218,6 +235,49 @@ int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col,
         ++s;
     }
     return s;
+}
+
+}  // namespace
+
+int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
+                           double alpha0, double growth, double L, double accept,
+                           int32_t *sigma, int32_t *pi) {
+    return growlocal_range(0, n, rowptr, col, k, alpha0, growth, L, accept, sigma, pi);
+}
+
+int32_t growlocal_blocks(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
+                         double alpha0, double growth, double L, double accept,
+                         int32_t blocks, int32_t threads, int32_t *sigma, int32_t *pi) {
+    if (blocks <= 1) return growlocal_schedule(n, rowptr, col, k, alpha0, growth, L, accept, sigma, pi);
+    auto bound = [&](int32_t b) { return int32_t(int64_t(b) * n / blocks); };
+    std::vector<int32_t> S(size_t(blocks), 0);
+    int32_t T = threads > 0 ? threads : int32_t(std::thread::hardware_concurrency());
+    T = std::max(1, std::min(T, blocks));
+    std::vector<std::exception_ptr> err(static_cast<size_t>(T));
+    auto work = [&](int32_t t) {
+        try {
+            for (int32_t b = t; b < blocks; b += T) {
+                const int32_t r0 = bound(b), r1 = bound(b + 1);
+                S[b] = growlocal_range(r0, r1, rowptr, col, k, alpha0, growth, L, accept, sigma + r0, pi + r0);
+            }
+        } catch (...) {
+            err[t] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(size_t(T) - 1);
+    for (int32_t t = 1; t < T; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
+    // concatenate: block b's supersteps follow those of blocks 0..b-1
+    int32_t offset = 0;
+    for (int32_t b = 0; b < blocks; ++b) {
+        for (int32_t v = bound(b); v < bound(b + 1); ++v) sigma[v] += offset;
+        offset += S[b];
+    }
+    return offset;
 }
 
 }  // namespace sptrsv

@@ -31,6 +31,8 @@ struct HostSchedule {
     int32_t mode = SPTRSV_SCHED_LEVELS;
     int32_t k = 1;
     int32_t S = 0;
+    int32_t sched_blocks = 1;        // diagonal blocks GrowLocal was run on (Sec. 3.1)
+    double schedule_ms = 0.0;        // host wall time of the superstep schedule alone
     std::vector<int32_t> level, sigma, pi;
     std::vector<int32_t> perm;       // Sec. 5 order: position -> original row
     std::vector<int32_t> dev_perm;   // device order: device row -> original row
@@ -118,6 +120,14 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
 int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
                            double alpha0, double growth, double L, double accept,
                            int32_t *sigma, int32_t *pi);
+// Block-parallel GrowLocal (Sec. 3.1): rows cut into `blocks` diagonal blocks of
+// floor(b n / blocks) .. floor((b+1) n / blocks) - 1, each block's sub-DAG
+// scheduled on one of `threads` host threads (0: one per hardware thread, at
+// most one per block), block schedules concatenated in block order.  blocks <= 1
+// is growlocal_schedule.  Returns the total number of supersteps.
+int32_t growlocal_blocks(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
+                         double alpha0, double growth, double L, double accept,
+                         int32_t blocks, int32_t threads, int32_t *sigma, int32_t *pi);
 // device.cu
 int upload_plan(sptrsv_plan *p, const sptrsv_csr *A);
 void free_device(sptrsv_plan *p);

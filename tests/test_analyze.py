@@ -234,3 +234,79 @@ def test_upper_validation_errors(L):
     with pytest.raises(sp.SptrsvError) as e:
         sp.Plan(W.laplace2d_lower(64, 8), device=-1, triangle="upper")   # a lower factor
     assert e.value.status in (sp.ERR_ZERO_DIAG, sp.ERR_NOT_LOWER)
+
+
+# ------------------------------------------------- block-parallel GrowLocal (Sec. 3.1)
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("blocks", [2, 3, 8, 22])
+def test_growlocal_blocks_bit_exact(L, name, blocks):
+    A = CASES[name]()
+    p = _host_plan(A, mode="growlocal", k=22, sched_blocks=blocks)
+    ex = p.export()
+    s, pi, S = oracle.growlocal_blocks(A, 22, blocks)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert np.array_equal(ex.perm, oracle.permutation(s, pi))
+    st = p.stats()
+    assert st["supersteps"] == S and st["sched_blocks"] == blocks
+    assert 0.0 <= st["schedule_ms"] <= st["analyze_ms"]
+    assert oracle.check_schedule(A, ex.sigma, ex.pi, 22) == []
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_growlocal_blocks_bit_exact_random_parameters(L, seed):
+    rng = np.random.default_rng(5000 + seed)
+    n = int(rng.integers(1, 3000))
+    A = (W.erdos_renyi_lower(n, float(rng.uniform(1e-4, 2e-2)), seed) if seed % 2 else
+         W.narrow_band_lower(n, float(rng.uniform(0.02, 0.2)), float(rng.uniform(3, 40)), seed))
+    k = int(rng.integers(1, 40))
+    blocks = int(rng.integers(1, 40))
+    threads = int(rng.integers(0, 6))
+    kw = dict(alpha0=float(rng.choice([1.0, 2.0, 20.0])), growth=float(rng.choice([1.2, 1.5, 2.0])),
+              L=float(rng.choice([0.0, 10.0, 500.0])), accept=float(rng.choice([0.9, 0.97, 1.0])))
+    p = _host_plan(A, mode="growlocal", k=k, sched_blocks=blocks, sched_threads=threads, **kw)
+    ex = p.export()
+    s, pi, S = oracle.growlocal_blocks(A, k, blocks, **kw)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert p.stats()["supersteps"] == S
+
+
+def test_growlocal_blocks_independent_of_threads(L):
+    A = W.random_window_lower(200_000, 6, 20000, 3)
+    ref = None
+    for threads in (1, 2, 3, 6, 0):
+        ex = _host_plan(A, mode="growlocal", k=152, sched_blocks=6, sched_threads=threads).export()
+        if ref is None:
+            ref = ex
+        assert np.array_equal(ex.sigma, ref.sigma) and np.array_equal(ex.pi, ref.pi)
+        assert np.array_equal(ex.perm, ref.perm)
+
+
+def test_growlocal_blocks_upper_factor(L):
+    # U = L^T is analysed as the reversed lower factor: its blocks cut the reversed rows
+    A = W.random_window_lower(20_000, 5, 3000, 4)
+    U = W.transpose(A)
+    p = _host_plan(U, mode="growlocal", k=16, sched_blocks=4, triangle="upper")
+    st = p.stats()
+    assert st["sched_blocks"] == 4 and st["supersteps"] >= 4
+    ex = p.export()
+    # every edge of U (row i waits on its columns j > i) respects Definition 2.1
+    rows = np.repeat(np.arange(U.n), np.diff(U.rowptr))
+    off = U.col != rows
+    u, v = U.col[off], rows[off]
+    assert np.all(ex.sigma[u] <= ex.sigma[v])
+    assert not np.any((ex.pi[u] != ex.pi[v]) & (ex.sigma[u] >= ex.sigma[v]))
+
+
+def test_sched_blocks_argument_errors(L):
+    A = W.laplace2d_lower(256, 16)
+    with pytest.raises(sp.SptrsvError) as e:
+        _host_plan(A, mode="levels", sched_blocks=4)
+    assert e.value.status == sp.ERR_ARG
+    for kw in (dict(sched_blocks=-1), dict(sched_threads=-2)):
+        with pytest.raises(sp.SptrsvError) as e:
+            _host_plan(A, mode="growlocal", k=4, **kw)
+        assert e.value.status == sp.ERR_ARG
+    # 0 and 1 both mean one schedule over the whole DAG
+    a = _host_plan(A, mode="growlocal", k=4, sched_blocks=0).export()
+    b = _host_plan(A, mode="growlocal", k=4, sched_blocks=1).export()
+    assert np.array_equal(a.sigma, b.sigma) and np.array_equal(a.pi, b.pi)

@@ -108,6 +108,26 @@ def test_f64_growlocal_parity(name, sync, k):
     assert oracle.rel_error(x, xo) <= F64_TOL
 
 
+@pytest.mark.parametrize("name", ["lap2d_64x64", "random_60k", "nb_20k"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local"])
+@pytest.mark.parametrize("blocks", [2, 6, 22])
+def test_f64_block_parallel_schedule_parity(name, sync, blocks):
+    # block-parallel GrowLocal (Sec. 3.1): schedule bit-exact, solve within FP64 tolerance
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=14)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A, mode="growlocal", k=152, sched_blocks=blocks)
+    ex = plan.export()
+    s, pi, S = oracle.growlocal_blocks(A, 152, blocks)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    x, rep = solve_gpu(plan, b, sync=sync)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+    xr, rep = solve_gpu(plan, b, precision="f32_refine")
+    assert rep["status"] == 0
+    assert oracle.rel_error(xr, xo) <= F64_TOL
+
+
 @pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0), (37, 3)])
 @pytest.mark.parametrize("rhs_tile", [0, 1, 4, 32])
