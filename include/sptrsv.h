@@ -53,7 +53,8 @@ enum {
     SPTRSV_ERR_TIMEOUT = -9,         /* a bounded device wait expired; x is invalid */
     SPTRSV_ERR_NOT_CONVERGED = -10,  /* refinement hit max_iters (x still returned) */
     SPTRSV_ERR_PENDING = -11,        /* serving request not finished yet            */
-    SPTRSV_ERR_NO_DEVICE = -12       /* plan was analysed host-only (device = -1)   */
+    SPTRSV_ERR_NO_DEVICE = -12,      /* plan was analysed host-only (device = -1)   */
+    SPTRSV_ERR_IO = -13              /* a saved plan could not be written or read   */
 };
 
 /* Name of a status code (static string). */
@@ -163,6 +164,32 @@ int sptrsv_plan_stats(const sptrsv_plan *plan, sptrsv_stats *out);
  *              (sorted by superstep, then core, then original id). */
 int sptrsv_plan_export(const sptrsv_plan *plan, int32_t *level, int32_t *sigma, int32_t *pi,
                        int32_t *perm);
+
+/* ------------------------------------------------------- saved plans */
+/* Write an analysed plan to `path` so that another process can rebuild it with
+ * sptrsv_plan_load without running the scheduler again: the file holds the
+ * factor `csr`, the superstep schedule (sigma, pi; Sec. 3) and, once a
+ * block-local solve has run, that executor's row partition.  The schedule and
+ * the partition depend only on the pattern, so the analysis cost (the paper's
+ * amortisation threshold, Table 7.6) is paid once per pattern.
+ *   csr  : the factor in the plan's triangle format, host memory; its pattern
+ *          must be the analysed one (checked: same wavefronts and the schedule
+ *          valid on it, Def. 2.1); its values are saved as given.
+ *   path : written through "<path>.tmp" and renamed.
+ * Format: little-endian binary, magic "SPTRSVPL", version 1, a checksum over
+ * the payload.  Errors: ARG (NULL, other size or pattern), IO (cannot write). */
+int sptrsv_plan_save(const sptrsv_plan *plan, const sptrsv_csr *csr, const char *path);
+
+/* Rebuild a saved plan.  opts->device and opts->values apply (NULL = defaults);
+ * the schedule, its mode, k and the triangle come from the file.  Nothing read
+ * is trusted: the factor is validated as in sptrsv_analyze, the schedule must
+ * satisfy Def. 2.1 on it (a wavefront schedule must equal the wavefronts), and
+ * a saved partition must list every block's rows in (wavefront, id) order, so a
+ * damaged file gives an error and never a plan that could stall a solve.
+ * Errors: IO (missing, truncated, wrong size), ARG (not a plan file, other
+ * version or byte order, checksum mismatch, invalid schedule or partition),
+ * the validation errors of sptrsv_analyze, OOM, CUDA. */
+int sptrsv_plan_load(const char *path, const sptrsv_analyze_opts *opts, sptrsv_plan **out);
 
 /* Host-only: the row -> thread block partition the block-local executor
  * (SPTRSV_SYNC_LOCAL) builds for `blocks` thread blocks, for inspection and

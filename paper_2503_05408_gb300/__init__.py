@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libsptrsv.so")
 OK = 0
 ERR_ARG, ERR_NOT_LOWER, ERR_UNSORTED_OR_DUP, ERR_ZERO_DIAG = -1, -2, -3, -4
 ERR_OOM, ERR_BUDGET, ERR_CUDA, ERR_LAUNCH, ERR_TIMEOUT = -5, -6, -7, -8, -9
-ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE = -10, -11, -12
+ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE, ERR_IO = -10, -11, -12, -13
 
 SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
 TRI_LOWER, TRI_UPPER, TRI_LOWER_TRANSPOSED = 0, 1, 2
@@ -122,6 +122,9 @@ def lib():
             "sptrsv_plan_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
             "sptrsv_plan_export": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "sptrsv_local_partition": (ctypes.c_int, [ctypes.POINTER(CSRStruct), i32, i32, vp, vp]),
+            "sptrsv_plan_save": (ctypes.c_int, [vp, ctypes.POINTER(CSRStruct), ctypes.c_char_p]),
+            "sptrsv_plan_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(AnalyzeOpts),
+                                                ctypes.POINTER(vp)]),
             "sptrsv_destroy": (None, [vp]),
             "sptrsv_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
             "sptrsv_solve": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
@@ -250,6 +253,30 @@ class Plan:
         self.n = int(A.n)
         self.device = int(device)
         del self._rowptr, self._col, self._val       # analyze copied what it needs
+
+    def save(self, A, path):
+        """Write this plan and the factor ``A`` (the one it was analysed from, in the
+        plan's triangle format) to ``path`` (``sptrsv_plan_save``)."""
+        rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        col = np.ascontiguousarray(A.col, dtype=np.int32)
+        val = np.ascontiguousarray(A.val, dtype=np.float64)
+        csr = CSRStruct(int(A.n), int(col.size), _ptr(rowptr), _ptr(col), _ptr(val))
+        _check(lib().sptrsv_plan_save(self.handle, ctypes.byref(csr), os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, values=VALUES_F64 | VALUES_F32, device=0):
+        """Rebuild a saved plan on ``device`` without scheduling again (``sptrsv_plan_load``)."""
+        lb = lib()
+        o = AnalyzeOpts()
+        lb.sptrsv_analyze_opts_default(ctypes.byref(o))
+        o.values, o.device = int(values), int(device)
+        h = ctypes.c_void_p()
+        _check(lb.sptrsv_plan_load(os.fsencode(path), ctypes.byref(o), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle = h.value
+        self.device = int(device)
+        self.n = self.stats()["n"]
+        return self
 
     def close(self):
         if self.handle:

@@ -257,7 +257,93 @@ bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<i
 }
 
 
-int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h) {
+// A saved schedule is accepted only if the executors can run it: supersteps
+// 0..S-1 all used, cores in [0, k), every edge into a later superstep or inside
+// one core's block (Def. 2.1); a wavefront schedule must be the wavefronts.
+int check_given(const sptrsv_csr *A, const HostSchedule &h, const GivenSchedule &g) {
+    const int32_t n = A->n;
+    if (g.S < 0 || g.k < 1 || (n > 0 && g.S < 1) || !(g.sigma && g.pi) && n > 0)
+        return fail(SPTRSV_ERR_ARG, "saved schedule: bad header");
+    std::vector<char> used(size_t(std::max(g.S, 1)), 0);
+    for (int32_t v = 0; v < n; ++v) {
+        if (g.sigma[v] < 0 || g.sigma[v] >= g.S || g.pi[v] < 0 || g.pi[v] >= g.k)
+            return fail(SPTRSV_ERR_ARG, "saved schedule: superstep or core out of range");
+        used[size_t(g.sigma[v])] = 1;
+    }
+    for (int32_t s = 0; s < g.S; ++s)
+        if (!used[size_t(s)]) return fail(SPTRSV_ERR_ARG, "saved schedule: supersteps not contiguous");
+    if (g.mode == SPTRSV_SCHED_LEVELS) {
+        if (g.S != h.nlevels) return fail(SPTRSV_ERR_ARG, "saved schedule: not the wavefronts");
+        for (int32_t v = 0; v < n; ++v)
+            if (g.sigma[v] != h.level[v] || g.pi[v] != 0)
+                return fail(SPTRSV_ERR_ARG, "saved schedule: not the wavefronts");
+        return SPTRSV_OK;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        const int32_t last = A->rowptr[v + 1] - 1;
+        for (int32_t q = A->rowptr[v]; q < last; ++q) {
+            const int32_t u = A->col[q];
+            if (g.sigma[u] > g.sigma[v] || (g.sigma[u] == g.sigma[v] && g.pi[u] != g.pi[v]))
+                return fail(SPTRSV_ERR_ARG, "saved schedule: violates Def. 2.1 on edge " + std::to_string(u) +
+                                                " -> " + std::to_string(v));
+        }
+    }
+    return SPTRSV_OK;
+}
+
+bool partition_valid(int32_t n, int32_t nb, const int32_t *blk, const int32_t *lidx, const std::vector<int32_t> &level) {
+    if (nb < 1 || (n > 0 && (!blk || !lidx))) return false;
+    std::vector<int32_t> load(size_t(nb), 0);
+    for (int32_t v = 0; v < n; ++v) {
+        if (blk[v] < 0 || blk[v] >= nb || lidx[v] < 0) return false;
+        load[size_t(blk[v])]++;
+    }
+    std::vector<int64_t> start(size_t(nb) + 1, 0);
+    for (int32_t b = 0; b < nb; ++b) start[b + 1] = start[b] + load[b];
+    std::vector<int32_t> at(size_t(n), -1);
+    for (int32_t v = 0; v < n; ++v) {
+        if (lidx[v] >= load[size_t(blk[v])]) return false;
+        int32_t &slot = at[size_t(start[blk[v]] + lidx[v])];
+        if (slot >= 0) return false;                        // two rows in one position
+        slot = v;
+    }
+    for (int32_t b = 0; b < nb; ++b)                         // (wavefront, id) order in each list
+        for (int64_t t = start[b] + 1; t < start[b + 1]; ++t) {
+            const int32_t u = at[size_t(t - 1)], v = at[size_t(t)];
+            if (level[u] > level[v] || (level[u] == level[v] && u > v)) return false;
+        }
+    return true;
+}
+
+int32_t factor_levels(const sptrsv_csr *A, std::vector<int32_t> &level) {
+    return A->n ? compute_levels(A, level) : (level.clear(), 0);
+}
+
+int lower_factor(const sptrsv_csr *csr, int32_t triangle, std::vector<int32_t> &rp, std::vector<int32_t> &col,
+                 std::vector<double> &val, sptrsv_csr &lowered, const sptrsv_csr **use) {
+    int st;
+    if (triangle == SPTRSV_TRI_UPPER) {
+        if ((st = validate_upper_csr(csr))) return st;
+        reverse_upper(csr, rp, col, val);
+    } else if (triangle == SPTRSV_TRI_LOWER_TRANSPOSED) {
+        if ((st = validate_csr(csr))) return st;
+        reverse_transpose(csr, rp, col, val);
+    } else if (triangle != SPTRSV_TRI_LOWER) {
+        return fail(SPTRSV_ERR_ARG, "unknown triangle");
+    }
+    *use = csr;
+    if (triangle != SPTRSV_TRI_LOWER) {
+        lowered.n = csr->n;
+        lowered.nnz = csr->nnz;
+        lowered.rowptr = rp.data();
+        lowered.col = col.data();
+        lowered.val = val.data();
+        *use = &lowered;
+    }
+    return validate_csr(*use);
+}
+
+int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h, const GivenSchedule *given) {
     const int32_t n = A->n;
     h.n = n;
     h.nnz = A->nnz;
@@ -272,7 +358,27 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
     h.sigma.assign(n, 0);
     h.pi.assign(n, 0);
     h.sched_blocks = 1;
-    if (o.mode == SPTRSV_SCHED_LEVELS) {
+    if (given) {
+        const auto t1 = std::chrono::steady_clock::now();
+        int st = check_given(A, h, *given);
+        if (st) return st;
+        h.mode = given->mode;
+        h.k = given->mode == SPTRSV_SCHED_LEVELS ? 1 : given->k;
+        h.S = given->S;
+        h.sched_blocks = std::max(1, given->sched_blocks);
+        if (n) {
+            std::memcpy(h.sigma.data(), given->sigma, size_t(n) * sizeof(int32_t));
+            std::memcpy(h.pi.data(), given->pi, size_t(n) * sizeof(int32_t));
+        }
+        if (given->loc_nb > 0) {
+            if (!partition_valid(n, given->loc_nb, given->loc_blk, given->loc_lidx, h.level))
+                return fail(SPTRSV_ERR_ARG, "saved block-local partition is not valid for this factor");
+            h.loc_nb = given->loc_nb;
+            h.loc_blk.assign(given->loc_blk, given->loc_blk + n);
+            h.loc_lidx.assign(given->loc_lidx, given->loc_lidx + n);
+        }
+        h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    } else if (o.mode == SPTRSV_SCHED_LEVELS) {
         h.k = 1;
         h.sigma = h.level;
         h.S = h.nlevels;
@@ -298,7 +404,7 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
     // Rows are visited in original order, which is topological.
     std::vector<int32_t> sub(n, 0);
     int32_t max_sub = 0;
-    if (o.mode != SPTRSV_SCHED_LEVELS) {
+    if (h.mode != SPTRSV_SCHED_LEVELS) {
         for (int32_t v = 0; v < n; ++v) {
             int32_t d = 0;
             const int32_t last = A->rowptr[v + 1] - 1;
@@ -377,6 +483,7 @@ const char *sptrsv_status_string(int status) {
         case SPTRSV_ERR_NOT_CONVERGED: return "SPTRSV_ERR_NOT_CONVERGED";
         case SPTRSV_ERR_PENDING: return "SPTRSV_ERR_PENDING";
         case SPTRSV_ERR_NO_DEVICE: return "SPTRSV_ERR_NO_DEVICE";
+        case SPTRSV_ERR_IO: return "SPTRSV_ERR_IO";
         default: return "SPTRSV_ERR_UNKNOWN";
     }
 }
@@ -407,6 +514,18 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     sptrsv_analyze_opts o;
     sptrsv_analyze_opts_default(&o);
     if (opts) o = *opts;
+    return analyze_impl(csr, o, nullptr, out);
+}
+
+}  // extern "C"
+
+int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const GivenSchedule *given,
+                         sptrsv_plan **out) {
+    if (given) {
+        o.mode = given->mode;
+        o.k = given->k;
+        o.sched_blocks = given->sched_blocks;
+    }
     if (o.values == 0) o.values = SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32;
     if (o.values & ~(SPTRSV_VALUES_F64 | SPTRSV_VALUES_F32)) return fail(SPTRSV_ERR_ARG, "bad values mask");
     if (o.device < -1) return fail(SPTRSV_ERR_ARG, "bad device");
@@ -422,25 +541,7 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     std::vector<int32_t> rrp, rcol;
     std::vector<double> rval;
     sptrsv_csr lowered;
-    int st;
-    if (o.triangle == SPTRSV_TRI_UPPER) {
-        if ((st = validate_upper_csr(csr))) return st;
-        reverse_upper(csr, rrp, rcol, rval);
-    } else if (o.triangle == SPTRSV_TRI_LOWER_TRANSPOSED) {
-        if ((st = validate_csr(csr))) return st;
-        reverse_transpose(csr, rrp, rcol, rval);
-    } else if (o.triangle != SPTRSV_TRI_LOWER) {
-        return fail(SPTRSV_ERR_ARG, "unknown triangle");
-    }
-    if (o.triangle != SPTRSV_TRI_LOWER) {
-        lowered.n = csr->n;
-        lowered.nnz = csr->nnz;
-        lowered.rowptr = rrp.data();
-        lowered.col = rcol.data();
-        lowered.val = rval.data();
-        csr = &lowered;
-    }
-    st = validate_csr(csr);
+    int st = lower_factor(csr, o.triangle, rrp, rcol, rval, lowered, &csr);
     if (st) return st;
     int32_t sms = 1;
     if (o.device >= 0) {
@@ -453,7 +554,7 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     sptrsv_plan *p = new (std::nothrow) sptrsv_plan();
     if (!p) return fail(SPTRSV_ERR_OOM, "host allocation failed");
     try {
-        st = build_schedule(csr, o, p->h);
+        st = build_schedule(csr, o, p->h, given);
     } catch (const std::bad_alloc &) {
         st = fail(SPTRSV_ERR_OOM, "host allocation failed during analysis");
     } catch (const std::exception &e) {           // e.g. a scheduling thread that could not start
@@ -466,6 +567,7 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     p->values = o.values;
     p->device = o.device;
     p->reversed = o.triangle != SPTRSV_TRI_LOWER;
+    p->triangle = o.triangle;
     for (int32_t i = 0; i < csr->n; ++i) {
         double rs = 0.0;
         for (int32_t q = csr->rowptr[i]; q < csr->rowptr[i + 1]; ++q) rs += std::abs(csr->val[q]);
@@ -485,6 +587,8 @@ int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrs
     *out = p;
     return SPTRSV_OK;
 }
+
+extern "C" {
 
 int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
     if (!p || !out) return fail(SPTRSV_ERR_ARG, "NULL argument");

@@ -388,9 +388,23 @@ int ensure_local(sptrsv_plan *p, int nb) {
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     const int32_t row_cap = int32_t((int64_t(optin) - 1024) / ((p->values & SPTRSV_VALUES_F64) ? 8 : 4));
     std::vector<int32_t> blk, lidx, load;
-    if (!local_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk, lidx, load))
-        return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the shared "
-                                        "memory of " + std::to_string(nb) + " blocks");
+    bool have = false;
+    if (h.loc_nb == nb && h.loc_blk.size() == size_t(n)) {         // built before, or read from a saved plan
+        blk = h.loc_blk;
+        lidx = h.loc_lidx;
+        load.assign(size_t(nb), 0);
+        for (int32_t v = 0; v < n; ++v) load[size_t(blk[v])]++;
+        have = *std::max_element(load.begin(), load.end()) <= row_cap;
+    }
+    if (!have) {
+        if (!local_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk, lidx,
+                             load))
+            return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the "
+                                            "shared memory of " + std::to_string(nb) + " blocks");
+        p->h.loc_nb = nb;
+        p->h.loc_blk = blk;
+        p->h.loc_lidx = lidx;
+    }
     std::vector<int32_t> bstart(size_t(nb) + 1, 0);
     for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
     // column ids in the block-local order: a parent of the same block -> its

@@ -33,6 +33,10 @@ struct HostSchedule {
     int32_t S = 0;
     int32_t sched_blocks = 1;        // diagonal blocks GrowLocal was run on (Sec. 3.1)
     double schedule_ms = 0.0;        // host wall time of the superstep schedule alone
+    // block-local executor partition, once built (or read from a saved plan):
+    // loc_blk[v] = block of row v, loc_lidx[v] = its position in the block's list
+    int32_t loc_nb = 0;
+    std::vector<int32_t> loc_blk, loc_lidx;
     std::vector<int32_t> level, sigma, pi;
     std::vector<int32_t> perm;       // Sec. 5 order: position -> original row
     std::vector<int32_t> dev_perm;   // device order: device row -> original row
@@ -84,6 +88,7 @@ struct sptrsv_plan {
     int32_t values = 0;
     int32_t device = -1;
     bool reversed = false;        // UPPER / LOWER_TRANSPOSED: analysed as L' with ids i' = n-1-i
+    int32_t triangle = SPTRSV_TRI_LOWER;
     int32_t num_sms = 0;
     int64_t nnz_off = 0;
     int32_t max_row_off = 0;      // most off-diagonal entries in one row
@@ -115,7 +120,26 @@ int validate_csr(const sptrsv_csr *A);
 bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
                      const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
                      std::vector<int32_t> &lidx, std::vector<int32_t> &load);
-int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h);
+// A schedule read from a saved plan instead of computed (analysed numbering).
+struct GivenSchedule {
+    int32_t mode = SPTRSV_SCHED_LEVELS, k = 1, S = 0, sched_blocks = 1;
+    const int32_t *sigma = nullptr, *pi = nullptr;
+    int32_t loc_nb = 0;                                  // saved block-local partition, if any
+    const int32_t *loc_blk = nullptr, *loc_lidx = nullptr;
+};
+int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedule &h,
+                   const GivenSchedule *given = nullptr);
+// sptrsv_analyze's body; `given` replaces the scheduler by a validated saved schedule.
+int analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const GivenSchedule *given, sptrsv_plan **out);
+// The lower factor a plan analyses: `csr` itself (LOWER) or L' numbered backwards
+// (UPPER, LOWER_TRANSPOSED) built in rp/col/val; validated.  *use points to it.
+int lower_factor(const sptrsv_csr *csr, int32_t triangle, std::vector<int32_t> &rp, std::vector<int32_t> &col,
+                 std::vector<double> &val, sptrsv_csr &lowered, const sptrsv_csr **use);
+// Wavefronts of a validated lower factor; returns their number.
+int32_t factor_levels(const sptrsv_csr *A, std::vector<int32_t> &level);
+// A saved block-local partition is usable: blocks in range, every block's list a
+// permutation of 0..load-1 in (wavefront, id) order.
+bool partition_valid(int32_t n, int32_t nb, const int32_t *blk, const int32_t *lidx, const std::vector<int32_t> &level);
 // growlocal.cpp
 int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
                            double alpha0, double growth, double L, double accept,

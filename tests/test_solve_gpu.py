@@ -377,3 +377,29 @@ def test_upper_full_size_3d():
     for sync in ("flags", "local"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert oracle.rel_error(x, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("name", ["random_60k", "lap3d_24"])
+@pytest.mark.parametrize("tri", ["lower", "upper"])
+def test_saved_plan_with_local_partition(tmp_path, name, tri):
+    # a block-local solve builds the partition; the saved plan carries it and the loaded
+    # plan solves with it (same x bits: same partition, same summation order)
+    A = SMALL[name]()
+    if tri == "upper":
+        A = W.transpose(A)
+    xs, b = W.manufactured_rhs(A, 1, seed=21)
+    xo = oracle.solve_upper(A, b) if tri == "upper" else oracle.solve(A, b)
+    plan = sp.Plan(A, mode="growlocal", k=152, sched_blocks=4, triangle=tri)
+    x1, rep = solve_gpu(plan, b, sync="local")
+    assert rep["status"] == 0 and oracle.rel_error(x1, xo) <= F64_TOL
+    path = tmp_path / "p.plan"
+    plan.save(A, path)
+    n, nnz = A.n, A.nnz
+    assert path.stat().st_size == 56 + (n + 1) * 4 + nnz * 12 + n * 8 + n * 8 + 8   # partition included
+    loaded = sp.Plan.load(path)
+    assert loaded.stats()["supersteps"] == plan.stats()["supersteps"]
+    x2, rep = solve_gpu(loaded, b, sync="local")
+    assert rep["status"] == 0
+    assert np.array_equal(x1, x2)
+    x3, rep = solve_gpu(loaded, b, sync="flags")
+    assert rep["status"] == 0 and oracle.rel_error(x3, xo) <= F64_TOL
