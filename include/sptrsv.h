@@ -109,7 +109,14 @@ typedef struct {
                           result does not depend on sched_threads.                        */
     int32_t sched_threads; /* host threads for the blocks; 0 = one per hardware thread,
                           never more than B                                               */
+    int32_t coarsen;   /* GROWLOCAL only, SPTRSV_COARSEN_*: FUNNEL schedules the DAG coarsened
+                          by in-funnels (Sec. 4, Algorithm 4.1) after dropping the long edge of
+                          every triangle u->v->w; each row takes its part's superstep and core.
+                          Not combined with sched_blocks > 1.                             */
+    double coarsen_max_weight;  /* largest part weight (stored entries of its rows) a part may
+                          grow to, the size constraint of Sec. 4.2; <= 0: 500 (= L)         */
 } sptrsv_analyze_opts;
+enum { SPTRSV_COARSEN_NONE = 0, SPTRSV_COARSEN_FUNNEL = 1 };
 
 /* The system a plan solves.  The method covers both substitution directions
  * (Sec. 2, Eq. 2.1 and its backward counterpart): an upper factor's DAG is the
@@ -124,7 +131,7 @@ typedef struct {
 enum { SPTRSV_TRI_LOWER = 0, SPTRSV_TRI_UPPER = 1, SPTRSV_TRI_LOWER_TRANSPOSED = 2 };
 
 /* Fill `o` with the defaults above (LEVELS, k = 0, 20, 1.5, 500, 0.97, both value
- * copies, device 0, LOWER, one schedule block, sched_threads 0). */
+ * copies, device 0, LOWER, one schedule block, sched_threads 0, no coarsening). */
 void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o);
 
 typedef struct {
@@ -142,6 +149,7 @@ typedef struct {
     double schedule_ms;      /* host wall time of the superstep schedule alone (part of
                                 analyze_ms): wavefronts for LEVELS, GrowLocal otherwise   */
     int32_t sched_blocks;    /* diagonal blocks the schedule was built on (1: whole DAG)    */
+    int32_t coarse_vertices; /* vertices of the DAG GrowLocal scheduled: Funnel parts, else n */
 } sptrsv_stats;
 
 /* Analyse a factor (Sec. 2.2 DAG, Sec. 1 wavefronts, Sec. 3 schedule, Sec. 5

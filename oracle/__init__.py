@@ -20,6 +20,9 @@ What it computes (each function cites the passage it follows):
 * ``growlocal``      the GrowLocal scheduler, Sec. 3 / Algorithm 3.1 (C)
 * ``growlocal_blocks``  block-parallel scheduling, Sec. 3.1: GrowLocal on each
   diagonal block's sub-DAG (full-row weights), block schedules concatenated
+* ``triangle_reduce``, ``funnel_parts``, ``funnel_growlocal``  Sec. 4: the
+  triangle transitive reduction, in-funnel coarsening (Algorithm 4.1) with a
+  part weight cap, and GrowLocal on the coarsened DAG
 * ``level_schedule`` sigma = wavefront, pi = 0 (the wavefront scheduler, Sec. 1)
 * ``check_schedule`` Definition 2.1 plus the bookkeeping rules of a schedule
 * ``permutation``    the reordering of Sec. 5: sort by (superstep, core, id)
@@ -247,9 +250,26 @@ def growlocal(A, k: int, alpha0: float = 20.0, growth: float = 1.5, L: float = 5
     return sigma, pi, int(S)
 
 
+def block_subdag(A, r0: int, r1: int):
+    """Sub-DAG of the diagonal block of rows r0..r1-1 (Sec. 3.1, Fig. 3.1): the
+    block's rows renumbered from 0 with only the entries in the block's own
+    columns (diagonal last), and every vertex's weight = its FULL row's entry
+    count.  Returns (rowptr, col, weight)."""
+    rp, c, _ = _arrays(A)
+    m = r1 - r0
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp[r0:r1 + 1]))
+    cols = c[rp[r0]:rp[r1]]
+    keep = cols >= r0                           # entries inside the diagonal block
+    sub_rp = np.zeros(m + 1, dtype=np.int32)
+    sub_rp[1:] = np.cumsum(np.bincount(rows[keep], minlength=m))
+    sub_col = np.ascontiguousarray(cols[keep] - r0, dtype=np.int32)
+    weight = np.ascontiguousarray(np.diff(rp[r0:r1 + 1]), dtype=np.int64)
+    return sub_rp, sub_col, weight
+
+
 def growlocal_blocks(A, k: int, blocks: int, alpha0: float = 20.0, growth: float = 1.5,
                      L: float = 500.0, accept: float = 0.97):
-    """Block-parallel scheduling (Sec. 3.1, Fig. 3.2), run one block after another.
+    """Block-parallel scheduling (Sec. 3.1, Fig. 3.1), run one block after another.
 
     The rows are cut into ``blocks`` diagonal blocks, block b holding rows
     floor(b n / blocks) .. floor((b+1) n / blocks) - 1 (the figure's equal
@@ -264,7 +284,6 @@ def growlocal_blocks(A, k: int, blocks: int, alpha0: float = 20.0, growth: float
     if k < 1:
         raise ValueError("k must be >= 1")
     lib = _load()
-    rp, c, _ = _arrays(A)
     n = A.n
     sigma = np.empty(n, dtype=np.int32)
     pi = np.empty(n, dtype=np.int32)
@@ -274,13 +293,7 @@ def growlocal_blocks(A, k: int, blocks: int, alpha0: float = 20.0, growth: float
         m = r1 - r0
         if m == 0:
             continue
-        rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp[r0:r1 + 1]))
-        cols = c[rp[r0]:rp[r1]]
-        keep = cols >= r0                       # entries inside the diagonal block
-        sub_rp = np.zeros(m + 1, dtype=np.int32)
-        sub_rp[1:] = np.cumsum(np.bincount(rows[keep], minlength=m))
-        sub_col = np.ascontiguousarray(cols[keep] - r0, dtype=np.int32)
-        weight = np.ascontiguousarray(np.diff(rp[r0:r1 + 1]), dtype=np.int64)   # full rows
+        sub_rp, sub_col, weight = block_subdag(A, r0, r1)
         s_b = np.empty(m, dtype=np.int32)
         p_b = np.empty(m, dtype=np.int32)
         S = lib.oracle_growlocal_weighted(m, _p(sub_rp, _i32p), _p(sub_col, _i32p), _p(weight, _i64p),
@@ -292,6 +305,108 @@ def growlocal_blocks(A, k: int, blocks: int, alpha0: float = 20.0, growth: float
         pi[r0:r1] = p_b
         offset += int(S)
     return sigma, pi, offset
+
+
+def triangle_reduce(A):
+    """Approximate transitive reduction used before coarsening (Sec. 4.2): every
+    edge (u, w) that is the long side of a triangle u -> v -> w of the DAG is
+    removed, all decided on the original edge set.  Returns the kept parents of
+    each vertex as a list of sorted int lists."""
+    n = A.n
+    par = [set(A.col[A.rowptr[i]:A.rowptr[i + 1] - 1].tolist()) for i in range(n)]
+    kept = []
+    for w in range(n):
+        long_edges = set()
+        for v in par[w]:
+            long_edges |= par[w] & par[v]          # u -> v -> w with u -> w also present
+        kept.append(sorted(par[w] - long_edges))
+    return kept
+
+
+def funnel_parts(n, parents, weight, max_weight):
+    """In-funnel coarsening, Algorithm 4.1 (Sec. 4.2), with the part weight cap.
+
+    Vertices are taken in reverse topological order (n-1 .. 0, the natural order
+    of a lower factor being topological); an unvisited vertex starts a part and
+    a priority queue (largest id first) grows it through parents all of whose
+    children already joined the part.  A popped vertex joins only while the
+    part's weight stays <= max_weight (a part's first vertex always joins).
+    Returns part[v] and the parts' roots in increasing root id."""
+    import heapq
+    children_count = [0] * n
+    outdeg = [0] * n
+    for w in range(n):
+        for u in parents[w]:
+            outdeg[u] += 1
+    visited = [False] * n
+    members_of = []
+    for v in range(n - 1, -1, -1):
+        if visited[v]:
+            continue
+        U, total = [], 0
+        touched = []
+        heap = [-v]
+        while heap:
+            w = -heapq.heappop(heap)
+            if U and total + weight[w] > max_weight:
+                continue                            # stays outside; starts its own part later
+            U.append(w)
+            total += weight[w]
+            for u in parents[w]:
+                children_count[u] += 1
+                touched.append(u)
+                if children_count[u] == outdeg[u]:
+                    heapq.heappush(heap, -u)
+        for u in touched:                           # ChildrenCount reset for the next part
+            children_count[u] = 0
+        for u in U:
+            visited[u] = True
+        members_of.append(U)
+    part = np.empty(n, dtype=np.int64)
+    roots = sorted(max(U) for U in members_of)
+    index = {r: i for i, r in enumerate(roots)}
+    for U in members_of:
+        part[U] = index[max(U)]
+    return part, roots
+
+
+def funnel_growlocal(A, k: int, max_weight: float = 500.0, reduce: bool = True, alpha0: float = 20.0,
+                     growth: float = 1.5, L: float = 500.0, accept: float = 0.97):
+    """Funnel + GrowLocal (Sec. 4): triangle reduction, in-funnel coarsening with
+    the weight cap, GrowLocal on the coarsened DAG (parts numbered by root, a
+    part weighing the sum of its rows' entries, an edge between two parts for
+    every kept edge between their members) and every vertex taking its part's
+    superstep and core.  Returns (sigma, pi, supersteps, part)."""
+    n = A.n
+    if n == 0:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32), 0, np.zeros(0, np.int64)
+    parents = triangle_reduce(A) if reduce else [A.col[A.rowptr[i]:A.rowptr[i + 1] - 1].tolist()
+                                                  for i in range(n)]
+    weight = np.diff(A.rowptr).astype(np.int64)
+    part, roots = funnel_parts(n, parents, weight.tolist(), max_weight)
+    m = len(roots)
+    cpar = [set() for _ in range(m)]
+    for w in range(n):
+        for u in parents[w]:
+            if part[u] != part[w]:
+                cpar[part[w]].add(int(part[u]))
+    crp = np.zeros(m + 1, dtype=np.int32)
+    ccol = []
+    for i in range(m):
+        assert all(j < i for j in cpar[i])          # root order is topological
+        ccol += sorted(cpar[i]) + [i]
+        crp[i + 1] = len(ccol)
+    ccol = np.array(ccol, dtype=np.int32)
+    cw = np.bincount(part, weights=weight, minlength=m).astype(np.int64)
+    s_c = np.empty(m, dtype=np.int32)
+    p_c = np.empty(m, dtype=np.int32)
+    lib = _load()
+    S = lib.oracle_growlocal_weighted(m, _p(crp, _i32p), _p(ccol, _i32p), _p(cw, _i64p), int(k),
+                                      float(alpha0), float(growth), float(L), float(accept),
+                                      _p(s_c, _i32p), _p(p_c, _i32p))
+    if S < 0:
+        raise MemoryError("oracle_growlocal_weighted failed")
+    return s_c[part].astype(np.int32), p_c[part].astype(np.int32), int(S), part
 
 
 def edges(A):

@@ -25,6 +25,8 @@ ERR_NOT_CONVERGED, ERR_PENDING, ERR_NO_DEVICE, ERR_IO = -10, -11, -12, -13
 SCHED_LEVELS, SCHED_GROWLOCAL = 0, 1
 TRI_LOWER, TRI_UPPER, TRI_LOWER_TRANSPOSED = 0, 1, 2
 _TRI = {"lower": TRI_LOWER, "upper": TRI_UPPER, "lower_transposed": TRI_LOWER_TRANSPOSED}
+COARSEN_NONE, COARSEN_FUNNEL = 0, 1
+_COARSEN = {"none": COARSEN_NONE, "funnel": COARSEN_FUNNEL}
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
 SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL = 0, 1, 2, 3, 4, 5
@@ -53,7 +55,8 @@ class AnalyzeOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha0", ctypes.c_double),
                 ("growth", ctypes.c_double), ("L", ctypes.c_double), ("accept", ctypes.c_double),
                 ("values", ctypes.c_int32), ("device", ctypes.c_int32), ("triangle", ctypes.c_int32),
-                ("sched_blocks", ctypes.c_int32), ("sched_threads", ctypes.c_int32)]
+                ("sched_blocks", ctypes.c_int32), ("sched_threads", ctypes.c_int32),
+                ("coarsen", ctypes.c_int32), ("coarsen_max_weight", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("supersteps", ctypes.c_int32), ("k", ctypes.c_int32), ("max_level_rows", ctypes.c_int32),
                 ("avg_wavefront", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("analyze_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("ring_rows", ctypes.c_int32),
-                ("schedule_ms", ctypes.c_double), ("sched_blocks", ctypes.c_int32)]
+                ("schedule_ms", ctypes.c_double), ("sched_blocks", ctypes.c_int32),
+                ("coarse_vertices", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -226,11 +230,13 @@ class Plan:
     ``triangle``: "lower" (L x = b), "upper" (U x = b, diagonal first in each row) or
     "lower_transposed" (L^T x = b from L's rows).
     ``sched_blocks`` > 1 (GrowLocal only): block-parallel scheduling (Sec. 3.1) on
-    ``sched_threads`` host threads (0: one per hardware thread)."""
+    ``sched_threads`` host threads (0: one per hardware thread).
+    ``coarsen="funnel"`` (GrowLocal only): schedule the Funnel-coarsened DAG (Sec. 4),
+    parts of weight <= ``coarsen_max_weight`` (0: 500)."""
 
     def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
                  values=VALUES_F64 | VALUES_F32, device=0, triangle="lower", sched_blocks=0,
-                 sched_threads=0):
+                 sched_threads=0, coarsen="none", coarsen_max_weight=0.0):
         lb = lib()
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         self._col = np.ascontiguousarray(A.col, dtype=np.int32)
@@ -246,6 +252,8 @@ class Plan:
         o.values, o.device = int(values), int(device)
         o.triangle = _TRI[triangle] if isinstance(triangle, str) else int(triangle)
         o.sched_blocks, o.sched_threads = int(sched_blocks), int(sched_threads)
+        o.coarsen = _COARSEN[coarsen] if isinstance(coarsen, str) else int(coarsen)
+        o.coarsen_max_weight = float(coarsen_max_weight)
         h = ctypes.c_void_p()
         self.handle = None
         _check(lb.sptrsv_analyze(ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))

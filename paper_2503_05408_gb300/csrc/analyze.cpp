@@ -366,6 +366,7 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
         h.k = given->mode == SPTRSV_SCHED_LEVELS ? 1 : given->k;
         h.S = given->S;
         h.sched_blocks = std::max(1, given->sched_blocks);
+        h.coarse_vertices = given->coarse_vertices > 0 ? given->coarse_vertices : n;
         if (n) {
             std::memcpy(h.sigma.data(), given->sigma, size_t(n) * sizeof(int32_t));
             std::memcpy(h.pi.data(), given->pi, size_t(n) * sizeof(int32_t));
@@ -382,13 +383,20 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
         h.k = 1;
         h.sigma = h.level;
         h.S = h.nlevels;
+        h.coarse_vertices = n;
         h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     } else if (o.mode == SPTRSV_SCHED_GROWLOCAL) {
         h.k = o.k;
         h.sched_blocks = std::max(1, o.sched_blocks);
         const auto t1 = std::chrono::steady_clock::now();
-        h.S = growlocal_blocks(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept, h.sched_blocks,
-                               o.sched_threads, h.sigma.data(), h.pi.data());
+        h.coarse_vertices = n;
+        if (o.coarsen == SPTRSV_COARSEN_FUNNEL)
+            h.S = funnel_growlocal(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept,
+                                   o.coarsen_max_weight > 0.0 ? o.coarsen_max_weight : 500.0, h.sigma.data(),
+                                   h.pi.data(), &h.coarse_vertices);
+        else
+            h.S = growlocal_blocks(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept, h.sched_blocks,
+                                   o.sched_threads, h.sigma.data(), h.pi.data());
         h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     } else {
         return fail(SPTRSV_ERR_ARG, "unknown schedule mode");
@@ -505,6 +513,8 @@ void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o) {
     o->triangle = SPTRSV_TRI_LOWER;
     o->sched_blocks = 0;
     o->sched_threads = 0;
+    o->coarsen = SPTRSV_COARSEN_NONE;
+    o->coarsen_max_weight = 0.0;
 }
 
 int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out) {
@@ -536,6 +546,10 @@ int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const Giv
     if (o.sched_blocks < 0 || o.sched_threads < 0) return fail(SPTRSV_ERR_ARG, "negative sched_blocks/threads");
     if (o.sched_blocks > 1 && o.mode != SPTRSV_SCHED_GROWLOCAL)
         return fail(SPTRSV_ERR_ARG, "sched_blocks > 1 needs the GROWLOCAL schedule");
+    if (o.coarsen != SPTRSV_COARSEN_NONE && o.coarsen != SPTRSV_COARSEN_FUNNEL)
+        return fail(SPTRSV_ERR_ARG, "unknown coarsen value");
+    if (o.coarsen == SPTRSV_COARSEN_FUNNEL && (o.mode != SPTRSV_SCHED_GROWLOCAL || o.sched_blocks > 1))
+        return fail(SPTRSV_ERR_ARG, "Funnel coarsening needs the GROWLOCAL schedule on one block");
     const auto t0 = std::chrono::steady_clock::now();
     // UPPER and LOWER_TRANSPOSED: analyse the lower factor L' numbered backwards
     std::vector<int32_t> rrp, rcol;
@@ -605,6 +619,7 @@ int sptrsv_plan_stats(const sptrsv_plan *p, sptrsv_stats *out) {
     out->ring_rows = p->h.ring_rows;
     out->schedule_ms = p->h.schedule_ms;
     out->sched_blocks = p->h.sched_blocks;
+    out->coarse_vertices = p->h.coarse_vertices;
     return SPTRSV_OK;
 }
 

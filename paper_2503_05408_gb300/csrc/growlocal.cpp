@@ -25,7 +25,7 @@
 //    one, or after a worthy attempt in which core 0 got fewer than floor(alpha)
 //    vertices (a larger alpha would repeat that attempt exactly).
 //
-// Block-parallel scheduling (Sec. 3.1, Fig. 3.2): the rows are cut into
+// Block-parallel scheduling (Sec. 3.1, Fig. 3.1): the rows are cut into
 // diagonal blocks, GrowLocal runs on each block's sub-DAG on its own host
 // thread, and the block schedules are concatenated.
 #include <algorithm>
@@ -57,8 +57,9 @@ struct Dag {
 
 // The sub-DAG of rows [r0, r1), numbered from 0.  Parents below r0 belong to
 // earlier blocks, which finish before this block starts, so their edges are
-// dropped; omega(v) stays the entry count of the full row (Sec. 3.1).
-Dag make_dag(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col) {
+// dropped; omega(v) stays the entry count of the full row (Sec. 3.1), unless
+// `weight` gives the weights (a coarsened DAG, Sec. 4).
+Dag make_dag(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col, const int64_t *weight) {
     Dag g;
     const int32_t n = r1 - r0;
     g.n = n;
@@ -67,7 +68,7 @@ Dag make_dag(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col) 
     g.indeg.assign(n, 0);
     for (int32_t v = 0; v < n; ++v) {
         const int32_t lo = rowptr[r0 + v], hi = rowptr[r0 + v + 1];
-        g.weight[v] = hi - lo;
+        g.weight[v] = weight ? weight[r0 + v] : hi - lo;
         for (int32_t q = lo; q < hi - 1; ++q)     // every stored entry but the diagonal
             if (col[q] >= r0) {
                 g.indeg[v]++;
@@ -206,11 +207,12 @@ class Scheduler {
 namespace {
 
 // GrowLocal on rows [r0, r1); sigma and pi are indexed by the block-local id.
-int32_t growlocal_range(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col, int32_t k,
-                        double alpha0, double growth, double L, double accept, int32_t *sigma, int32_t *pi) {
+int32_t growlocal_range(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col, const int64_t *weight,
+                        int32_t k, double alpha0, double growth, double L, double accept, int32_t *sigma,
+                        int32_t *pi) {
     const int32_t n = r1 - r0;
     if (n <= 0) return 0;
-    Dag g = make_dag(r0, r1, rowptr, col);
+    Dag g = make_dag(r0, r1, rowptr, col, weight);
     Scheduler sch(g, k);
     std::vector<char> done(n, 0);
     std::vector<int32_t> keep_v, keep_p;
@@ -242,7 +244,12 @@ int32_t growlocal_range(int32_t r0, int32_t r1, const int32_t *rowptr, const int
 int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
                            double alpha0, double growth, double L, double accept,
                            int32_t *sigma, int32_t *pi) {
-    return growlocal_range(0, n, rowptr, col, k, alpha0, growth, L, accept, sigma, pi);
+    return growlocal_range(0, n, rowptr, col, nullptr, k, alpha0, growth, L, accept, sigma, pi);
+}
+
+int32_t growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col, const int64_t *weight, int32_t k,
+                           double alpha0, double growth, double L, double accept, int32_t *sigma, int32_t *pi) {
+    return growlocal_range(0, n, rowptr, col, weight, k, alpha0, growth, L, accept, sigma, pi);
 }
 
 int32_t growlocal_blocks(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
@@ -258,7 +265,8 @@ int32_t growlocal_blocks(int32_t n, const int32_t *rowptr, const int32_t *col, i
         try {
             for (int32_t b = t; b < blocks; b += T) {
                 const int32_t r0 = bound(b), r1 = bound(b + 1);
-                S[b] = growlocal_range(r0, r1, rowptr, col, k, alpha0, growth, L, accept, sigma + r0, pi + r0);
+                S[b] = growlocal_range(r0, r1, rowptr, col, nullptr, k, alpha0, growth, L, accept, sigma + r0,
+                                       pi + r0);
             }
         } catch (...) {
             err[t] = std::current_exception();

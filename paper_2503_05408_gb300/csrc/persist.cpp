@@ -10,7 +10,7 @@
 //   uint32   order      0x01020304 as written by the saving host
 //   int32    n, triangle
 //   int64    nnz
-//   int32    mode, k, supersteps, sched_blocks, loc_nb, reserved
+//   int32    mode, k, supersteps, sched_blocks, loc_nb, coarse_vertices
 //   int32    rowptr[n + 1], col[nnz]; double val[nnz]   the caller's factor
 //   int32    sigma[n], pi[n]                           analysed numbering
 //   int32    loc_blk[n], loc_lidx[n]                   only if loc_nb > 0
@@ -36,7 +36,7 @@ struct Header {
     uint32_t version, order;
     int32_t n, triangle;
     int64_t nnz;
-    int32_t mode, k, S, sched_blocks, loc_nb, reserved;
+    int32_t mode, k, S, sched_blocks, loc_nb, coarse;
 };
 static_assert(sizeof(Header) == 56, "saved plan header layout");
 
@@ -114,6 +114,7 @@ int sptrsv_plan_save(const sptrsv_plan *p, const sptrsv_csr *csr, const char *pa
     hd.S = h.S;
     hd.sched_blocks = h.sched_blocks;
     hd.loc_nb = part ? h.loc_nb : 0;
+    hd.coarse = h.coarse_vertices;
     const std::string tmp = std::string(path) + ".tmp";
     File out;
     out.f = std::fopen(tmp.c_str(), "wb");
@@ -219,6 +220,7 @@ int load_body(FILE *f, const Header &hd, const sptrsv_analyze_opts *opts, sptrsv
     g.k = hd.k;
     g.S = hd.S;
     g.sched_blocks = hd.sched_blocks;
+    g.coarse_vertices = hd.coarse;
     g.sigma = sigma.data();
     g.pi = pi.data();
     g.loc_nb = hd.loc_nb;

@@ -32,6 +32,7 @@ struct HostSchedule {
     int32_t k = 1;
     int32_t S = 0;
     int32_t sched_blocks = 1;        // diagonal blocks GrowLocal was run on (Sec. 3.1)
+    int32_t coarse_vertices = 0;     // vertices of the scheduled DAG (Funnel parts, else n)
     double schedule_ms = 0.0;        // host wall time of the superstep schedule alone
     // block-local executor partition, once built (or read from a saved plan):
     // loc_blk[v] = block of row v, loc_lidx[v] = its position in the block's list
@@ -122,7 +123,7 @@ bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<i
                      std::vector<int32_t> &lidx, std::vector<int32_t> &load);
 // A schedule read from a saved plan instead of computed (analysed numbering).
 struct GivenSchedule {
-    int32_t mode = SPTRSV_SCHED_LEVELS, k = 1, S = 0, sched_blocks = 1;
+    int32_t mode = SPTRSV_SCHED_LEVELS, k = 1, S = 0, sched_blocks = 1, coarse_vertices = 0;
     const int32_t *sigma = nullptr, *pi = nullptr;
     int32_t loc_nb = 0;                                  // saved block-local partition, if any
     const int32_t *loc_blk = nullptr, *loc_lidx = nullptr;
@@ -144,6 +145,15 @@ bool partition_valid(int32_t n, int32_t nb, const int32_t *blk, const int32_t *l
 int32_t growlocal_schedule(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k,
                            double alpha0, double growth, double L, double accept,
                            int32_t *sigma, int32_t *pi);
+// GrowLocal with explicit vertex weights (a coarsened DAG).
+int32_t growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col, const int64_t *weight, int32_t k,
+                           double alpha0, double growth, double L, double accept, int32_t *sigma, int32_t *pi);
+// funnel.cpp: Funnel + GrowLocal (Sec. 4): triangle transitive reduction, in-funnel
+// coarsening with parts of weight <= max_weight, GrowLocal on the coarsened DAG,
+// each row taking its part's superstep and core.  *parts = coarsened vertices.
+int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k, double alpha0,
+                         double growth, double L, double accept, double max_weight, int32_t *sigma, int32_t *pi,
+                         int32_t *parts);
 // Block-parallel GrowLocal (Sec. 3.1): rows cut into `blocks` diagonal blocks of
 // floor(b n / blocks) .. floor((b+1) n / blocks) - 1, each block's sub-DAG
 // scheduled on one of `threads` host threads (0: one per hardware thread, at

@@ -310,3 +310,60 @@ def test_sched_blocks_argument_errors(L):
     a = _host_plan(A, mode="growlocal", k=4, sched_blocks=0).export()
     b = _host_plan(A, mode="growlocal", k=4, sched_blocks=1).export()
     assert np.array_equal(a.sigma, b.sigma) and np.array_equal(a.pi, b.pi)
+
+
+# ------------------------------------------------------ Funnel coarsening (Sec. 4)
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("max_weight", [0.5, 40.0, 500.0])
+def test_funnel_growlocal_bit_exact(L, name, max_weight):
+    A = CASES[name]()
+    p = _host_plan(A, mode="growlocal", k=22, coarsen="funnel", coarsen_max_weight=max_weight)
+    ex = p.export()
+    s, pi, S, part = oracle.funnel_growlocal(A, 22, max_weight=max_weight)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert np.array_equal(ex.perm, oracle.permutation(s, pi))
+    st = p.stats()
+    assert st["supersteps"] == S
+    assert st["coarse_vertices"] == (int(part.max()) + 1 if A.n else 0)
+    assert oracle.check_schedule(A, ex.sigma, ex.pi, 22) == []
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_funnel_growlocal_bit_exact_random_parameters(L, seed):
+    rng = np.random.default_rng(7000 + seed)
+    n = int(rng.integers(1, 2500))
+    A = (W.erdos_renyi_lower(n, float(rng.uniform(1e-4, 2e-2)), seed) if seed % 3 == 0 else
+         W.narrow_band_lower(n, float(rng.uniform(0.02, 0.5)), float(rng.uniform(2, 40)), seed) if seed % 3 == 1
+         else W.random_window_lower(n, int(rng.integers(1, 8)), int(rng.integers(4, 500)), seed))
+    k = int(rng.integers(1, 40))
+    cap = float(rng.choice([1.0, 7.0, 100.0, 500.0, 5000.0]))
+    kw = dict(alpha0=float(rng.choice([1.0, 5.0, 20.0])), growth=float(rng.choice([1.2, 1.5])),
+              L=float(rng.choice([0.0, 50.0, 500.0])), accept=float(rng.choice([0.9, 0.97])))
+    p = _host_plan(A, mode="growlocal", k=k, coarsen="funnel", coarsen_max_weight=cap, **kw)
+    ex = p.export()
+    s, pi, S, part = oracle.funnel_growlocal(A, k, max_weight=cap, **kw)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    assert p.stats()["supersteps"] == S
+
+
+def test_funnel_default_weight_and_errors(L):
+    A = W.erdos_renyi_lower(3000, 1e-3, 2)
+    a = _host_plan(A, mode="growlocal", k=8, coarsen="funnel").export()
+    b = _host_plan(A, mode="growlocal", k=8, coarsen="funnel", coarsen_max_weight=500.0).export()
+    assert np.array_equal(a.sigma, b.sigma) and np.array_equal(a.pi, b.pi)
+    for kw in (dict(mode="levels", coarsen="funnel"), dict(mode="growlocal", k=4, coarsen="funnel", sched_blocks=3),
+               dict(mode="growlocal", k=4, coarsen=7)):
+        with pytest.raises(sp.SptrsvError) as e:
+            _host_plan(A, **kw)
+        assert e.value.status == sp.ERR_ARG
+    st = _host_plan(A, mode="growlocal", k=8).stats()
+    assert st["coarse_vertices"] == A.n
+
+
+def test_funnel_plan_round_trips_through_a_file(L, tmp_path):
+    A = W.narrow_band_lower(6000, 0.05, 20, 3)
+    p = _host_plan(A, mode="growlocal", k=16, coarsen="funnel")
+    p.save(A, tmp_path / "f.plan")
+    q = sp.Plan.load(tmp_path / "f.plan", device=-1)
+    assert np.array_equal(p.export().sigma, q.export().sigma)
+    assert q.stats()["coarse_vertices"] == p.stats()["coarse_vertices"] < A.n

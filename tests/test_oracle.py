@@ -297,6 +297,34 @@ def test_growlocal_every_vertex_once_on_er_100k():
 
 
 # ------------------------------------------------- block-parallel GrowLocal (Sec. 3.1)
+def test_block_subdags_match_fig3_1():
+    # Three blocks of the 9x9 example: the equal-row cut reproduces the figure's blocks,
+    # each sub-DAG holds exactly the figure's solid (intra-block) edges, the dropped
+    # entries are its dashed (inter-block) dependencies, and weights stay full-row.
+    g = golden("fig3_1.txt")
+    n, ents = _pattern_from_golden(g)
+    A = W.from_pattern(n, ents)
+    blocks = [tuple(int(t) - 1 for t in b.split("-")) for b in g["blocks"].split()]
+    want_intra = [sorted(tuple(int(t) - 1 for t in e.split(",")) for e in part.split())
+                  for part in g["intra"].split("|")]
+    dropped = set()
+    for b, (lo, hi) in enumerate(blocks):
+        r0, r1 = b * n // 3, (b + 1) * n // 3
+        assert (r0, r1 - 1) == (lo, hi)
+        rp, col, w = oracle.block_subdag(A, r0, r1)
+        got = []
+        for i in range(r1 - r0):
+            assert col[rp[i + 1] - 1] == i                    # diagonal kept, last
+            got += [(int(col[q]) + r0, i + r0) for q in range(rp[i], rp[i + 1] - 1)]
+        assert sorted(got) == want_intra[b]
+        assert w.tolist() == np.diff(A.rowptr)[r0:r1].tolist()
+        for i in range(r0, r1):
+            for q in range(A.rowptr[i], A.rowptr[i + 1] - 1):
+                if A.col[q] < r0:
+                    dropped.add((int(A.col[q]) // 3, b))
+    assert dropped == {tuple(int(t) - 1 for t in e.split(",")) for e in g["inter"].split()}
+
+
 def test_growlocal_blocks_hand_example_full_row_weights():
     # Rows 0..3: diagonal only (weight 1).  Row 4 <- {0,1,2,3} (weight 5), rows 5..7
     # diagonal only.  Two blocks {0..3}, {4..7}; k = 2, alpha0 = 1, growth = 2, L = 0.
@@ -379,6 +407,105 @@ def test_growlocal_blocks_valid_and_block_ordered(seed):
         assert seg.min() == lo
         lo = int(seg.max()) + 1
     assert S == lo
+
+
+# -------------------------------------------------- Funnel coarsening (Sec. 4)
+def _digraph(n, parents):
+    G = nx.DiGraph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from((u, w) for w in range(n) for u in parents[w])
+    return G
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_triangle_reduce_brute_force(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(1, 13))
+    A = W.erdos_renyi_lower(n, float(rng.uniform(0.1, 0.7)), seed)
+    full = [set(A.col[A.rowptr[i]:A.rowptr[i + 1] - 1].tolist()) for i in range(n)]
+    kept = oracle.triangle_reduce(A)
+    for w in range(n):
+        want = {u for u in full[w] if not any(u in full[v] for v in full[w])}
+        assert set(kept[w]) == want and kept[w] == sorted(kept[w])
+    # the reduction keeps reachability: same transitive closure as the DAG
+    G, R = _digraph(n, [sorted(f) for f in full]), _digraph(n, kept)
+    assert set(nx.transitive_closure_dag(G).edges) == set(nx.transitive_closure_dag(R).edges)
+
+
+def test_funnel_hand_examples():
+    inf = float("inf")
+    # diamond 0 -> {1, 2} -> 3: one in-funnel rooted at 3
+    part, roots = oracle.funnel_parts(4, [[], [0], [0], [1, 2]], [1, 2, 2, 3], inf)
+    assert part.tolist() == [0, 0, 0, 0] and roots == [3]
+    # an in-tree is an in-funnel (Sec. 4.2 footnote): 0,1 -> 2; 3 -> 4; 2,4 -> 5
+    part, roots = oracle.funnel_parts(6, [[], [], [0, 1], [], [3], [2, 4]], [1] * 6, inf)
+    assert part.tolist() == [0] * 6 and roots == [5]
+    # a vertex with children in two parts joins neither: 0 -> 1, 0 -> 2
+    part, roots = oracle.funnel_parts(3, [[], [0], [0]], [1, 2, 2], inf)
+    assert roots == [0, 1, 2] and part.tolist() == [0, 1, 2]
+    # weight cap 4 on the chain 0 -> 1 -> 2 -> 3 (weights 1, 2, 2, 2): {2, 3} fills the
+    # first part (1 would make it 6), {0, 1} the second; parts numbered by root
+    part, roots = oracle.funnel_parts(4, [[], [0], [1], [2]], [1, 2, 2, 2], 4)
+    assert part.tolist() == [0, 0, 1, 1] and roots == [1, 3]
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_funnel_parts_are_in_funnels_and_coarsening_is_acyclic(seed):
+    rng = np.random.default_rng(1300 + seed)
+    n = int(rng.integers(1, 40))
+    A = (W.erdos_renyi_lower(n, float(rng.uniform(0.03, 0.4)), seed) if seed % 2 else
+         W.narrow_band_lower(n, float(rng.uniform(0.2, 0.9)), float(rng.uniform(1, 4)), seed))
+    kept = oracle.triangle_reduce(A)
+    weight = np.diff(A.rowptr).tolist()
+    cap = float(rng.choice([3, 8, 1e9]))
+    part, roots = oracle.funnel_parts(n, kept, weight, cap)
+    assert sorted(set(part.tolist())) == list(range(len(roots)))
+    R = _digraph(n, kept)
+    reach = nx.transitive_closure_dag(R)
+    for i, r in enumerate(roots):
+        U = set(np.nonzero(part == i)[0].tolist())
+        assert max(U) == r
+        out_cut = {u for u in U if any(w not in U for w in R.successors(u))}
+        in_cut = {v for v in U if any(u not in U for u in R.predecessors(v))}
+        assert out_cut <= {r}                                   # Def. in-funnel: one exit at most
+        assert all(v == u or reach.has_edge(v, u) for v in in_cut for u in out_cut)   # cascade
+        if len(U) > 1:
+            assert sum(weight[u] for u in U) <= cap
+    # Prop. (cascade coarsening): the ORIGINAL DAG coarsened along the parts is acyclic
+    u, v = oracle.edges(A)
+    C = nx.DiGraph()
+    C.add_nodes_from(range(len(roots)))
+    C.add_edges_from((int(part[a]), int(part[b])) for a, b in zip(u, v) if part[a] != part[b])
+    assert nx.is_directed_acyclic_graph(C)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_funnel_growlocal_schedule_valid(seed):
+    rng = np.random.default_rng(1700 + seed)
+    n = int(rng.integers(1, 600))
+    A = W.erdos_renyi_lower(n, float(rng.uniform(0.002, 0.05)), seed)
+    k = int(rng.integers(1, 9))
+    sigma, pi, S, part = oracle.funnel_growlocal(A, k, max_weight=float(rng.choice([4.0, 50.0, 500.0])),
+                                                 alpha0=float(rng.choice([1.0, 20.0])))
+    assert oracle.check_schedule(A, sigma, pi, k) == []
+    for i in range(int(part.max()) + 1 if n else 0):           # a part never straddles a block
+        members = part == i
+        assert len(set(sigma[members])) == 1 and len(set(pi[members])) == 1
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.erdos_renyi_lower(500, 0.01, 3),
+    lambda: W.laplace2d_lower(400, 20),
+    lambda: W.narrow_band_lower(500, 0.1, 8, 4),
+])
+def test_funnel_growlocal_without_coarsening_is_growlocal(make):
+    # max_weight 0: every part is one vertex; without the reduction the coarsened DAG is
+    # the DAG itself, so the schedule must be GrowLocal's
+    A = make()
+    sigma, pi, S, part = oracle.funnel_growlocal(A, 6, max_weight=0.0, reduce=False)
+    s, p, S2 = oracle.growlocal(A, 6)
+    assert np.array_equal(part, np.arange(A.n))
+    assert np.array_equal(sigma, s) and np.array_equal(pi, p) and S == S2
 
 
 # ---------------------------------------------------------------- permutation

@@ -128,6 +128,25 @@ def test_f64_block_parallel_schedule_parity(name, sync, blocks):
     assert oracle.rel_error(xr, xo) <= F64_TOL
 
 
+@pytest.mark.parametrize("name", ["er_30k", "nb_20k", "lap2d_64x64"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local"])
+@pytest.mark.parametrize("max_weight", [40.0, 500.0])
+def test_f64_funnel_schedule_parity(name, sync, max_weight):
+    # Funnel + GrowLocal (Sec. 4): schedule bit-exact, solve within FP64 tolerance
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=15)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A, mode="growlocal", k=152, coarsen="funnel", coarsen_max_weight=max_weight)
+    ex = plan.export()
+    s, pi, S, part = oracle.funnel_growlocal(A, 152, max_weight=max_weight)
+    assert np.array_equal(ex.sigma, s) and np.array_equal(ex.pi, pi)
+    x, rep = solve_gpu(plan, b, sync=sync)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+    if sync == "grid":
+        assert rep["barriers"] <= S - 1
+
+
 @pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0), (37, 3)])
 @pytest.mark.parametrize("rhs_tile", [0, 1, 4, 32])
@@ -383,14 +402,17 @@ def test_upper_full_size_3d():
 @pytest.mark.parametrize("tri", ["lower", "upper"])
 def test_saved_plan_with_local_partition(tmp_path, name, tri):
     # a block-local solve builds the partition; the saved plan carries it and the loaded
-    # plan solves with it (same x bits: same partition, same summation order)
+    # plan solves with it.  Same x bits with one entry per lane (32 lanes, rows of at most
+    # 32 entries): then no lane's partial sum depends on the order its parents arrive in,
+    # so equal bits mean the same partition and the same summation order.
     A = SMALL[name]()
     if tri == "upper":
         A = W.transpose(A)
     xs, b = W.manufactured_rhs(A, 1, seed=21)
     xo = oracle.solve_upper(A, b) if tri == "upper" else oracle.solve(A, b)
     plan = sp.Plan(A, mode="growlocal", k=152, sched_blocks=4, triangle=tri)
-    x1, rep = solve_gpu(plan, b, sync="local")
+    det = dict(sync="local", lanes=32, threads=1024, eager_sum=2)
+    x1, rep = solve_gpu(plan, b, **det)
     assert rep["status"] == 0 and oracle.rel_error(x1, xo) <= F64_TOL
     path = tmp_path / "p.plan"
     plan.save(A, path)
@@ -398,8 +420,10 @@ def test_saved_plan_with_local_partition(tmp_path, name, tri):
     assert path.stat().st_size == 56 + (n + 1) * 4 + nnz * 12 + n * 8 + n * 8 + 8   # partition included
     loaded = sp.Plan.load(path)
     assert loaded.stats()["supersteps"] == plan.stats()["supersteps"]
-    x2, rep = solve_gpu(loaded, b, sync="local")
+    x2, rep = solve_gpu(loaded, b, **det)
     assert rep["status"] == 0
     assert np.array_equal(x1, x2)
+    x4, rep = solve_gpu(loaded, b, sync="local")
+    assert rep["status"] == 0 and oracle.rel_error(x4, xo) <= F64_TOL
     x3, rep = solve_gpu(loaded, b, sync="flags")
     assert rep["status"] == 0 and oracle.rel_error(x3, xo) <= F64_TOL
