@@ -115,6 +115,11 @@ typedef struct {
                           Not combined with sched_blocks > 1.                             */
     double coarsen_max_weight;  /* largest part weight (stored entries of its rows) a part may
                           grow to, the size constraint of Sec. 4.2; <= 0: 500 (= L)         */
+    int32_t analyze_on_device; /* 1: LEVELS schedule of a LOWER factor analysed on `device`:
+                          wavefronts by a polled kernel, the Sec. 5 order by a stable radix
+                          sort, the device layout by gathers, from one upload of the CSR;
+                          the plan equals the host analysis bit for bit (validation and the
+                          one-block ring test stay on the host).  0: host analysis.          */
 } sptrsv_analyze_opts;
 enum { SPTRSV_COARSEN_NONE = 0, SPTRSV_COARSEN_FUNNEL = 1 };
 
@@ -131,7 +136,8 @@ enum { SPTRSV_COARSEN_NONE = 0, SPTRSV_COARSEN_FUNNEL = 1 };
 enum { SPTRSV_TRI_LOWER = 0, SPTRSV_TRI_UPPER = 1, SPTRSV_TRI_LOWER_TRANSPOSED = 2 };
 
 /* Fill `o` with the defaults above (LEVELS, k = 0, 20, 1.5, 500, 0.97, both value
- * copies, device 0, LOWER, one schedule block, sched_threads 0, no coarsening). */
+ * copies, device 0, LOWER, one schedule block, sched_threads 0, no coarsening, host
+ * analysis). */
 void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o);
 
 typedef struct {

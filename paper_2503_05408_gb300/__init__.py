@@ -56,7 +56,8 @@ class AnalyzeOpts(ctypes.Structure):
                 ("growth", ctypes.c_double), ("L", ctypes.c_double), ("accept", ctypes.c_double),
                 ("values", ctypes.c_int32), ("device", ctypes.c_int32), ("triangle", ctypes.c_int32),
                 ("sched_blocks", ctypes.c_int32), ("sched_threads", ctypes.c_int32),
-                ("coarsen", ctypes.c_int32), ("coarsen_max_weight", ctypes.c_double)]
+                ("coarsen", ctypes.c_int32), ("coarsen_max_weight", ctypes.c_double),
+                ("analyze_on_device", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -232,11 +233,13 @@ class Plan:
     ``sched_blocks`` > 1 (GrowLocal only): block-parallel scheduling (Sec. 3.1) on
     ``sched_threads`` host threads (0: one per hardware thread).
     ``coarsen="funnel"`` (GrowLocal only): schedule the Funnel-coarsened DAG (Sec. 4),
-    parts of weight <= ``coarsen_max_weight`` (0: 500)."""
+    parts of weight <= ``coarsen_max_weight`` (0: 500).
+    ``analyze_on_device=True`` (LEVELS, lower): wavefronts, order and layout computed
+    by kernels on ``device``."""
 
     def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
                  values=VALUES_F64 | VALUES_F32, device=0, triangle="lower", sched_blocks=0,
-                 sched_threads=0, coarsen="none", coarsen_max_weight=0.0):
+                 sched_threads=0, coarsen="none", coarsen_max_weight=0.0, analyze_on_device=False):
         lb = lib()
         self._rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
         self._col = np.ascontiguousarray(A.col, dtype=np.int32)
@@ -254,6 +257,7 @@ class Plan:
         o.sched_blocks, o.sched_threads = int(sched_blocks), int(sched_threads)
         o.coarsen = _COARSEN[coarsen] if isinstance(coarsen, str) else int(coarsen)
         o.coarsen_max_weight = float(coarsen_max_weight)
+        o.analyze_on_device = int(bool(analyze_on_device))
         h = ctypes.c_void_p()
         self.handle = None
         _check(lb.sptrsv_analyze(ctypes.byref(csr), ctypes.byref(o), ctypes.byref(h)))

@@ -315,6 +315,8 @@ bool partition_valid(int32_t n, int32_t nb, const int32_t *blk, const int32_t *l
     return true;
 }
 
+int32_t ring_rows_of(const sptrsv_csr *A, const HostSchedule &h) { return ring_window(A, h); }
+
 int32_t factor_levels(const sptrsv_csr *A, std::vector<int32_t> &level) {
     return A->n ? compute_levels(A, level) : (level.clear(), 0);
 }
@@ -515,6 +517,7 @@ void sptrsv_analyze_opts_default(sptrsv_analyze_opts *o) {
     o->sched_threads = 0;
     o->coarsen = SPTRSV_COARSEN_NONE;
     o->coarsen_max_weight = 0.0;
+    o->analyze_on_device = 0;
 }
 
 int sptrsv_analyze(const sptrsv_csr *csr, const sptrsv_analyze_opts *opts, sptrsv_plan **out) {
@@ -550,6 +553,10 @@ int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const Giv
         return fail(SPTRSV_ERR_ARG, "unknown coarsen value");
     if (o.coarsen == SPTRSV_COARSEN_FUNNEL && (o.mode != SPTRSV_SCHED_GROWLOCAL || o.sched_blocks > 1))
         return fail(SPTRSV_ERR_ARG, "Funnel coarsening needs the GROWLOCAL schedule on one block");
+    if (o.analyze_on_device != 0 && o.analyze_on_device != 1) return fail(SPTRSV_ERR_ARG, "bad analyze_on_device");
+    if (o.analyze_on_device && !given &&
+        (o.mode != SPTRSV_SCHED_LEVELS || o.triangle != SPTRSV_TRI_LOWER || o.device < 0))
+        return fail(SPTRSV_ERR_ARG, "device analysis covers the wavefront schedule of a LOWER factor on a device");
     const auto t0 = std::chrono::steady_clock::now();
     // UPPER and LOWER_TRANSPOSED: analyse the lower factor L' numbered backwards
     std::vector<int32_t> rrp, rcol;
@@ -567,6 +574,26 @@ int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const Giv
 
     sptrsv_plan *p = new (std::nothrow) sptrsv_plan();
     if (!p) return fail(SPTRSV_ERR_OOM, "host allocation failed");
+    if (o.analyze_on_device && !given && csr->n > 0) {
+        p->values = o.values;
+        p->device = o.device;
+        p->triangle = o.triangle;
+        p->num_sms = sms;
+        p->nnz_off = csr->nnz - csr->n;
+        try {
+            st = analyze_levels_device(p, csr, o.device, o.values);
+        } catch (const std::bad_alloc &) {
+            st = fail(SPTRSV_ERR_OOM, "host allocation failed during analysis");
+        }
+        if (st) {
+            free_device(p);
+            delete p;
+            return st;
+        }
+        p->analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = p;
+        return SPTRSV_OK;
+    }
     try {
         st = build_schedule(csr, o, p->h, given);
     } catch (const std::bad_alloc &) {

@@ -136,6 +136,11 @@ int analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const GivenSchedu
 // (UPPER, LOWER_TRANSPOSED) built in rp/col/val; validated.  *use points to it.
 int lower_factor(const sptrsv_csr *csr, int32_t triangle, std::vector<int32_t> &rp, std::vector<int32_t> &col,
                  std::vector<double> &val, sptrsv_csr &lowered, const sptrsv_csr **use);
+// Smallest safe shared-memory x ring of a one-block walk (0: none), as build_schedule sets it.
+int32_t ring_rows_of(const sptrsv_csr *A, const HostSchedule &h);
+// analyze_gpu.cu: the wavefront schedule, its Sec. 5 order and the device layout
+// computed on `device` from the caller's lower CSR (validated); fills p->h and p->d.
+int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values);
 // Wavefronts of a validated lower factor; returns their number.
 int32_t factor_levels(const sptrsv_csr *A, std::vector<int32_t> &level);
 // A saved block-local partition is usable: blocks in range, every block's list a
