@@ -309,8 +309,10 @@ def run_ours(args):
     A, xs, b_np = spec["make"]()
     nrhs = spec["nrhs"]
     t0 = time.perf_counter()
-    plan = sp.Plan(A, mode=args.schedule, device=local, triangle=spec.get("triangle", "lower"),
-                   sched_blocks=args.sched_blocks, sched_threads=args.sched_threads)
+    triangle = spec.get("triangle", "lower")
+    on_device = args.schedule == "levels" and triangle == "lower"      # wavefront plans: device analysis
+    plan = sp.Plan(A, mode=args.schedule, device=local, triangle=triangle, sched_blocks=args.sched_blocks,
+                   sched_threads=args.sched_threads, analyze_on_device=on_device)
     analyze_s = time.perf_counter() - t0
     st = plan.stats()
 
@@ -401,6 +403,7 @@ def run_ours(args):
                    "nrhs": nrhs, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
                    "levels": st["levels"], "supersteps": st["supersteps"], "schedule": args.schedule,
                    "sched_blocks": st["sched_blocks"], "schedule_ms": st["schedule_ms"],
+                   "analysis": "device" if on_device else "host",
                    "sync": rep["sync_name"], "lanes": rep["lanes"], "grid": rep["grid"],
                    "threads": rep["threads"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -330,6 +330,16 @@ int scan(const int32_t *in, int32_t *out, int64_t m, int32_t *tile_sum, AnaCtl *
     return SPTRSV_OK;
 }
 
+// Block-local layout values: entry q of the block-local order is device-order
+// entry src[q], row t is device row rsrc[t].
+template <typename T>
+__global__ void k_local_values(int64_t nnz_off, int32_t n, const int32_t *src, const int32_t *rsrc, const T *val,
+                               const T *dinv, T *lval, T *ldinv) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < nnz_off; q += stride) lval[q] = val[src[q]];
+    for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n; t += stride) ldinv[t] = dinv[rsrc[t]];
+}
+
 struct SetDevice {
     int prev = -1;
     explicit SetDevice(int dev) {
@@ -501,6 +511,34 @@ int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32
     bytes += int64_t(std::max<size_t>(size_t(n), 1) * sizeof(uint32_t));
     p->device_bytes = bytes;
     (void)t0;
+    return SPTRSV_OK;
+}
+
+int local_values_device(sptrsv_plan *p, const std::vector<int32_t> &src, const std::vector<int32_t> &rsrc,
+                        int64_t *bytes) {
+    DeviceBuffers &d = p->d;
+    const int64_t nnz_off = int64_t(src.size());
+    const int32_t n = int32_t(rsrc.size());
+    Temps tmp;
+    int32_t *g_src, *g_rsrc;
+    int st;
+    if ((st = tmp.get(&g_src, size_t(nnz_off))) || (st = tmp.get(&g_rsrc, size_t(n)))) return st;
+    if (nnz_off) ANA_TRY(cudaMemcpy(g_src, src.data(), size_t(nnz_off) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (n) ANA_TRY(cudaMemcpy(g_rsrc, rsrc.data(), size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((std::max<int64_t>(nnz_off, n) + 255) / 256, 4096)));
+    if (d.val) {
+        if ((st = alloc_zeroed(&d.l_val, size_t(nnz_off), bytes)) || (st = alloc_zeroed(&d.l_dinv, size_t(n), bytes)))
+            return st;
+        k_local_values<double><<<grid, 256>>>(nnz_off, n, g_src, g_rsrc, d.val, d.dinv, d.l_val, d.l_dinv);
+    }
+    if (d.s32) {
+        if ((st = alloc_zeroed(&d.l_s32, size_t(nnz_off), bytes)) ||
+            (st = alloc_zeroed(&d.l_dinv32, size_t(n), bytes)))
+            return st;
+        k_local_values<float><<<grid, 256>>>(nnz_off, n, g_src, g_rsrc, d.s32, d.dinv32, d.l_s32, d.l_dinv32);
+    }
+    ANA_TRY(cudaGetLastError());
+    ANA_TRY(cudaDeviceSynchronize());                  // the temporaries are freed on return
     return SPTRSV_OK;
 }
 

@@ -430,19 +430,12 @@ int ensure_local(sptrsv_plan *p, int nb) {
     if ((st = upload(lrp, &d.l_rp, &bytes)) || (st = upload(lcol, &d.l_col, &bytes)) ||
         (st = upload(lperm_out, &d.l_perm, &bytes)) || (st = upload(bstart, &d.l_blk_row, &bytes)))
         return st;
-    // values: a gather of the device-order arrays into the block-local order
-    auto regather = [&](auto *dval, auto *ddiag, auto **lval, auto **ldiag) -> int {
-        using V = std::remove_pointer_t<decltype(dval)>;
-        std::vector<V> hv, hd, ov(nnz), od(n);
-        int s2;
-        if ((s2 = download(dval, nnz, hv)) || (s2 = download(ddiag, size_t(n), hd))) return s2;
-        for (size_t q = 0; q < nnz; ++q) ov[q] = hv[size_t(src[q])];
-        for (int32_t t = 0; t < n; ++t) od[t] = hd[dev_of[lperm[t]]];
-        if ((s2 = upload(ov, lval, &bytes)) || (s2 = upload(od, ldiag, &bytes))) return s2;
-        return SPTRSV_OK;
-    };
-    if (d.val && (st = regather(d.val, d.dinv, &d.l_val, &d.l_dinv))) return st;
-    if (d.s32 && (st = regather(d.s32, d.dinv32, &d.l_s32, &d.l_dinv32))) return st;
+    // values: gathered on the device from the device-order arrays into the block-local order
+    {
+        std::vector<int32_t> rsrc(n);
+        for (int32_t t = 0; t < n; ++t) rsrc[t] = dev_of[lperm[t]];
+        if ((st = local_values_device(p, src, rsrc, &bytes))) return st;
+    }
     d.loc_nb = nb;
     d.loc_smem = size_t(maxrows) * size_t((p->values & SPTRSV_VALUES_F64) ? 8 : 4);
     d.loc_bytes = bytes;

@@ -141,6 +141,11 @@ int32_t ring_rows_of(const sptrsv_csr *A, const HostSchedule &h);
 // analyze_gpu.cu: the wavefront schedule, its Sec. 5 order and the device layout
 // computed on `device` from the caller's lower CSR (validated); fills p->h and p->d.
 int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values);
+// analyze_gpu.cu: the block-local layout's values gathered on the device from the
+// device-order arrays (entry q <- src[q], row t <- rsrc[t]); allocates l_val/l_dinv
+// and/or l_s32/l_dinv32 as the plan holds FP64 and/or FP32 values.
+int local_values_device(sptrsv_plan *p, const std::vector<int32_t> &src, const std::vector<int32_t> &rsrc,
+                        int64_t *bytes);
 // Wavefronts of a validated lower factor; returns their number.
 int32_t factor_levels(const sptrsv_csr *A, std::vector<int32_t> &level);
 // A saved block-local partition is usable: blocks in range, every block's list a
