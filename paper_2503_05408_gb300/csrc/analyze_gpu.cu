@@ -38,7 +38,7 @@ constexpr int kTile = kThreads * kItems;       // keys per sort / scan tile
 struct AnaCtl {
     int32_t status;                 // 0, or SPTRSV_ERR_TIMEOUT from k_levels
     int32_t maxlevel;               // deepest wavefront
-    uint32_t cursor;                // next row to claim
+    uint32_t cursor;                // unused
     int32_t max_row_off;            // most off-diagonal entries in a row
     unsigned long long lnorm_bits;  // max row sum |A_ij| (non-negative double as bits)
     int32_t total;                  // scan total
@@ -54,17 +54,18 @@ __device__ __forceinline__ void st_level(int32_t *p, int32_t v) {
     asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// level[] starts at -1.  A warp claims the next row, its lanes wait on the row's
-// parents (all claimed earlier, so every wait ends while the grid is co-resident)
-// and lane 0 publishes 1 + the deepest parent's wavefront.
+// level[] starts at -1.  Rows are dealt round-robin to the warps of a co-resident
+// grid and taken in increasing order; a warp's lanes wait on the row's parents and
+// lane 0 publishes 1 + the deepest parent's wavefront.  Every wait ends: the
+// warp owning the smallest unfinished row has finished its earlier rows, so it is
+// at that row, whose parents (smaller ids) are all finished.
 __global__ void __launch_bounds__(kThreads) k_levels(int32_t n, const int32_t *rp, const int32_t *col,
                                                      int32_t *level, AnaCtl *c, long long timeout_ns) {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        int32_t row = 0;
-        if (lane == 0) row = int32_t(atomicAdd(&c->cursor, 1u));
-        row = __shfl_sync(0xffffffffu, row, 0);
-        if (row >= n) return;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    int32_t deepest = -1;                            // this warp's deepest row, one atomic at the end
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < n; r += warps) {
+        const int32_t row = int32_t(r);
         const int32_t lo = rp[row], last = rp[row + 1] - 1;
         int32_t d = 0;
         bool bad = false;
@@ -90,11 +91,10 @@ __global__ void __launch_bounds__(kThreads) k_levels(int32_t n, const int32_t *r
             return;
         }
         d = __reduce_max_sync(0xffffffffu, d);
-        if (lane == 0) {
-            st_level(level + row, d);
-            atomicMax(&c->maxlevel, d);
-        }
+        if (lane == 0) st_level(level + row, d);
+        deepest = max(deepest, d);
     }
+    if (lane == 0 && deepest >= 0) atomicMax(&c->maxlevel, deepest);
 }
 
 // Histogram of one 8-bit digit per tile, stored digit-major: hist[digit * ntiles + tile].
@@ -259,6 +259,8 @@ __global__ void __launch_bounds__(kThreads) k_layout(int32_t n, const int32_t *r
                                                      LayoutOut o, AnaCtl *c) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    unsigned long long norm_bits = 0;               // this warp's maxima, one atomic each at the end
+    int32_t widest = 0;
     for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < n; r += warps) {
         const int32_t v = perm[r];
         const int32_t lo = rp[v], last = rp[v + 1] - 1, dst = drp[r];
@@ -286,9 +288,13 @@ __global__ void __launch_bounds__(kThreads) k_layout(int32_t n, const int32_t *r
             }
             double rs = 0.0;
             for (int32_t q = lo; q <= last; ++q) rs = __dadd_rn(rs, fabs(val[q]));
-            atomicMax(&c->lnorm_bits, static_cast<unsigned long long>(__double_as_longlong(rs)));
-            atomicMax(&c->max_row_off, last - lo);
+            norm_bits = max(norm_bits, static_cast<unsigned long long>(__double_as_longlong(rs)));
+            widest = max(widest, last - lo);
         }
+    }
+    if (lane == 0) {
+        atomicMax(&c->lnorm_bits, norm_bits);
+        atomicMax(&c->max_row_off, widest);
     }
 }
 

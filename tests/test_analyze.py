@@ -367,3 +367,13 @@ def test_funnel_plan_round_trips_through_a_file(L, tmp_path):
     q = sp.Plan.load(tmp_path / "f.plan", device=-1)
     assert np.array_equal(p.export().sigma, q.export().sigma)
     assert q.stats()["coarse_vertices"] == p.stats()["coarse_vertices"] < A.n
+
+
+def test_device_analysis_argument_errors_on_host(L):
+    # refused before any device call: wrong schedule, wrong triangle, no device
+    A = W.laplace2d_lower(256, 16)
+    for B, kw in ((A, dict(mode="growlocal", k=4, device=-1)), (W.transpose(A), dict(triangle="upper", device=-1)),
+                  (A, dict(device=-1))):
+        with pytest.raises(sp.SptrsvError) as e:
+            sp.Plan(B, analyze_on_device=True, **kw)
+        assert e.value.status == sp.ERR_ARG
