@@ -109,3 +109,17 @@ def test_device_analysis_argument_errors():
     with pytest.raises(sp.SptrsvError) as e:
         sp.Plan(bad, analyze_on_device=True)
     assert e.value.status == sp.ERR_ZERO_DIAG
+
+
+def test_device_analysed_plan_saves_and_loads(tmp_path):
+    A = W.random_window_lower(50_000, 6, 5000, 7)
+    dev = sp.Plan(A, mode="levels", analyze_on_device=True)
+    xs, b = W.manufactured_rhs(A, 1, seed=33)
+    x1 = _solve(dev, b, sync="local", lanes=32, threads=1024, eager_sum=2)      # builds the partition
+    dev.save(A, tmp_path / "d.plan")
+    q = sp.Plan.load(tmp_path / "d.plan")
+    for f in ("level", "sigma", "pi", "perm"):
+        assert np.array_equal(getattr(dev.export(), f), getattr(q.export(), f)), f
+    x2 = _solve(q, b, sync="local", lanes=32, threads=1024, eager_sum=2)
+    assert np.array_equal(x1, x2)
+    assert oracle.rel_error(x2[:, None], oracle.solve(A, b)) <= 1e-12

@@ -147,6 +147,21 @@ def test_f64_funnel_schedule_parity(name, sync, max_weight):
         assert rep["barriers"] <= S - 1
 
 
+@pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
+@pytest.mark.parametrize("sched", [dict(coarsen="funnel"), dict(sched_blocks=5)])
+@pytest.mark.parametrize("sync", ["grid", "flags", "local"])
+def test_backward_substitution_with_funnel_and_blocks(tri, sched, sync):
+    # the other direction (Sec. 2) under the Sec. 3.1 / Sec. 4 schedules of the reversed DAG
+    L = W.make_dominant(W.narrow_band_lower(20_000, 0.05, 20, 5))
+    A = W.transpose(L) if tri == "upper" else L
+    xs, b = W.manufactured_rhs(W.transpose(L), 1, seed=16)
+    xo = oracle.solve_upper(W.transpose(L), b)
+    plan = sp.Plan(A, mode="growlocal", k=152, triangle=tri, **sched)
+    x, rep = solve_gpu(plan, b, sync=sync)
+    assert rep["status"] == 0
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
 @pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs"])
 @pytest.mark.parametrize("nrhs,ld_pad", [(2, 0), (5, 7), (32, 0), (37, 3)])
 @pytest.mark.parametrize("rhs_tile", [0, 1, 4, 32])
