@@ -1,7 +1,10 @@
 /*
- * sptrsv.h - C ABI of a GB300 (sm_103a) sparse lower-triangular solver that
- * executes forward substitution according to a superstep schedule of the
- * factor's dependency DAG.
+ * sptrsv.h - C ABI of a GB300 (sm_103a) sparse triangular solver that
+ * executes forward (and backward) substitution according to a superstep
+ * schedule of the factor's dependency DAG: wavefronts, GrowLocal, its
+ * block-parallel form or GrowLocal on the Funnel-coarsened DAG; analysis on
+ * the host or (wavefronts) on the device; plans saved to and loaded from
+ * files; single, batched and served solves.
  *
  * Method: arXiv:2503.05408, "Efficient parallel scheduling for sparse
  * triangular solvers".  Citations below name the paper's sections,
