@@ -38,7 +38,7 @@ constexpr int kTile = kThreads * kItems;       // keys per sort / scan tile
 struct AnaCtl {
     int32_t status;                 // 0, or SPTRSV_ERR_TIMEOUT from k_levels
     int32_t maxlevel;               // deepest wavefront
-    uint32_t cursor;                // unused
+    uint32_t pad0;
     int32_t max_row_off;            // most off-diagonal entries in a row
     unsigned long long lnorm_bits;  // max row sum |A_ij| (non-negative double as bits)
     int32_t total;                  // scan total
@@ -456,7 +456,7 @@ int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32
         o.dlo = d.diag_lo;
         o.dinv32 = d.dinv32;
     }
-    k_layout<<<std::max(1, std::min((n + 7) / 8, 152 * 8)), kThreads>>>(n, g_rp, g_col, g_val, perm, d.rp, o, c);
+    k_layout<<<std::max(1, std::min((n + 7) / 8, sms * 8)), kThreads>>>(n, g_rp, g_col, g_val, perm, d.rp, o, c);
     k_phase_ent<<<std::max(1, std::min((S + 1 + 255) / 256, 1024)), 256>>>(start, S + 1, d.rp, d.phase_ent);
     ANA_TRY(cudaGetLastError());
     ANA_TRY(cudaMemcpy(d.perm, perm, size_t(n) * sizeof(int32_t), cudaMemcpyDeviceToDevice));

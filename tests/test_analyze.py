@@ -377,3 +377,21 @@ def test_device_analysis_argument_errors_on_host(L):
         with pytest.raises(sp.SptrsvError) as e:
             sp.Plan(B, analyze_on_device=True, **kw)
         assert e.value.status == sp.ERR_ARG
+
+
+@pytest.mark.parametrize("kw", [dict(coarsen="funnel"), dict(sched_blocks=3), dict(sched_blocks=5, sched_threads=2)])
+def test_new_schedules_on_degenerate_factors(L, kw):
+    # empty factor: no supersteps; one row: one superstep; more blocks than rows allowed
+    empty = _host_plan(W.from_pattern(0, []), mode="growlocal", k=4, **kw)
+    assert empty.stats()["supersteps"] == 0 and empty.stats()["coarse_vertices"] == 0
+    one = W.from_pattern(1, [])
+    p = _host_plan(one, mode="growlocal", k=4, **kw)
+    assert p.export().sigma.tolist() == [0] and p.stats()["supersteps"] == 1
+    two = W.from_pattern(2, [(1, 0)])
+    p = _host_plan(two, mode="growlocal", k=4, **kw)
+    ex = p.export()
+    if "coarsen" in kw:
+        s, pi, S, _ = oracle.funnel_growlocal(two, 4)
+    else:
+        s, pi, S = oracle.growlocal_blocks(two, 4, kw["sched_blocks"])
+    assert ex.sigma.tolist() == s.tolist() and ex.pi.tolist() == pi.tolist()
