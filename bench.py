@@ -473,7 +473,7 @@ def run_batch(args):
     factors = [W.batch_factor(f) for f in range(count)]
     nrhs = 8
     rhs = [W.manufactured_rhs(A, nrhs, seed=7000 + i) for i, A in enumerate(factors)]
-    plans = [sp.Plan(A, device=local) for A in factors]
+    plans = [sp.Plan(A, device=local, analyze_on_device=True) for A in factors]
     bs = [_colmajor_dev(b, dev) for _, b in rhs]
     xs = [torch.empty_strided(b.shape, b.stride(), dtype=torch.float64, device=dev) for b in bs]
     precision = args.precision or "f32_refine"
@@ -587,7 +587,7 @@ def _serve_setup(local, nfactors=64):
     g = torch.Generator(device=dev)
     for f in range(nfactors):
         A = W.serve_factor(f)
-        plans.append(sp.Plan(A, device=local))
+        plans.append(sp.Plan(A, device=local, analyze_on_device=True))
         g.manual_seed(9000 + f)
         xs = (torch.rand((16, A.n), generator=g, device=dev, dtype=torch.float64) * 2 - 1).T   # col-major
         L = torch.sparse_csr_tensor(torch.from_numpy(A.rowptr.astype(np.int64)),

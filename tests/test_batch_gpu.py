@@ -116,3 +116,26 @@ def test_batch_mixes_lower_and_upper_plans():
     torch.cuda.synchronize()
     for x, ref in zip(xs_, refs):
         assert O.rel_error(x.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32_refine"])
+def test_batch_over_device_analysed_plans(precision):
+    # plans analysed on the device are the host plans bit for bit: the batch runs them the same way
+    factors = [W.batch_factor(f) for f in range(12)]
+    nrhs = [1, 3, 8, 2] * 3
+    host = [sp.Plan(A) for A in factors]
+    dev = [sp.Plan(A, analyze_on_device=True) for A in factors]
+    rhs = [W.manufactured_rhs(A, r, seed=400 + i) for i, (A, r) in enumerate(zip(factors, nrhs))]
+    out = []
+    for plans in (host, dev):
+        batch = sp.Batch(plans, nrhs, precision=precision)
+        bs = [colmajor(b) for _, b in rhs]
+        xs = [torch.full_like(b, float("nan")) for b in bs]
+        reps = batch.run(bs, xs)
+        torch.cuda.synchronize()
+        assert all(r["status"] == 0 for r in reps)
+        out.append([x.cpu().numpy().reshape(A.n, -1) for x, A in zip(xs, factors)])
+    for A, (_, b), xh, xd in zip(factors, rhs, out[0], out[1]):
+        xo = oracle.solve(A, b)
+        assert oracle.rel_error(xd, xo) <= F64_TOL
+        assert oracle.rel_error(xh, xo) <= F64_TOL
