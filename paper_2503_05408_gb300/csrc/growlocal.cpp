@@ -34,6 +34,7 @@
 #include <exception>
 #include <functional>
 #include <queue>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -274,8 +275,14 @@ int32_t growlocal_blocks(int32_t n, const int32_t *rowptr, const int32_t *col, i
     };
     std::vector<std::thread> pool;
     pool.reserve(size_t(T) - 1);
-    for (int32_t t = 1; t < T; ++t) pool.emplace_back(work, t);
+    int32_t started = 1;
+    try {
+        for (; started < T; ++started) pool.emplace_back(work, started);
+    } catch (const std::system_error &) {
+        // no more threads: this thread also takes the shares that found none
+    }
     work(0);
+    for (int32_t t = started; t < T; ++t) work(t);
     for (auto &th : pool) th.join();
     for (auto &e : err)
         if (e) std::rethrow_exception(e);
