@@ -311,7 +311,7 @@ def run_ours(args):
     nrhs = spec["nrhs"]
     t0 = time.perf_counter()
     triangle = spec.get("triangle", "lower")
-    on_device = args.schedule == "levels" and triangle == "lower"      # wavefront plans: device analysis
+    on_device = args.schedule == "levels"                              # wavefront plans: device analysis
     plan = sp.Plan(A, mode=args.schedule, device=local, triangle=triangle, sched_blocks=args.sched_blocks,
                    sched_threads=args.sched_threads, analyze_on_device=on_device)
     analyze_s = time.perf_counter() - t0

@@ -118,7 +118,8 @@ typedef struct {
                           Not combined with sched_blocks > 1.                             */
     double coarsen_max_weight;  /* largest part weight (stored entries of its rows) a part may
                           grow to, the size constraint of Sec. 4.2; <= 0: 500 (= L)         */
-    int32_t analyze_on_device; /* 1: LEVELS schedule of a LOWER factor analysed on `device`:
+    int32_t analyze_on_device; /* 1: LEVELS schedule analysed on `device` (any triangle; UPPER and
+                          LOWER_TRANSPOSED are reversed on the host first):
                           wavefronts by a polled kernel, the Sec. 5 order by a stable radix
                           sort, the device layout by gathers, from one upload of the CSR;
                           the plan equals the host analysis bit for bit (validation and the

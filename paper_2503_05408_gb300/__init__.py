@@ -234,8 +234,8 @@ class Plan:
     ``sched_threads`` host threads (0: one per hardware thread).
     ``coarsen="funnel"`` (GrowLocal only): schedule the Funnel-coarsened DAG (Sec. 4),
     parts of weight <= ``coarsen_max_weight`` (0: 500).
-    ``analyze_on_device=True`` (LEVELS, lower): wavefronts, order and layout computed
-    by kernels on ``device``."""
+    ``analyze_on_device=True`` (LEVELS): wavefronts, order and layout computed by kernels
+    on ``device``."""
 
     def __init__(self, A, mode="levels", k=0, alpha0=20.0, growth=1.5, L=500.0, accept=0.97,
                  values=VALUES_F64 | VALUES_F32, device=0, triangle="lower", sched_blocks=0,

@@ -554,9 +554,8 @@ int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const Giv
     if (o.coarsen == SPTRSV_COARSEN_FUNNEL && (o.mode != SPTRSV_SCHED_GROWLOCAL || o.sched_blocks > 1))
         return fail(SPTRSV_ERR_ARG, "Funnel coarsening needs the GROWLOCAL schedule on one block");
     if (o.analyze_on_device != 0 && o.analyze_on_device != 1) return fail(SPTRSV_ERR_ARG, "bad analyze_on_device");
-    if (o.analyze_on_device && !given &&
-        (o.mode != SPTRSV_SCHED_LEVELS || o.triangle != SPTRSV_TRI_LOWER || o.device < 0))
-        return fail(SPTRSV_ERR_ARG, "device analysis covers the wavefront schedule of a LOWER factor on a device");
+    if (o.analyze_on_device && !given && (o.mode != SPTRSV_SCHED_LEVELS || o.device < 0))
+        return fail(SPTRSV_ERR_ARG, "device analysis covers the wavefront schedule, on a device");
     const auto t0 = std::chrono::steady_clock::now();
     // UPPER and LOWER_TRANSPOSED: analyse the lower factor L' numbered backwards
     std::vector<int32_t> rrp, rcol;
@@ -578,10 +577,11 @@ int sptrsv::analyze_impl(const sptrsv_csr *csr, sptrsv_analyze_opts o, const Giv
         p->values = o.values;
         p->device = o.device;
         p->triangle = o.triangle;
+        p->reversed = o.triangle != SPTRSV_TRI_LOWER;
         p->num_sms = sms;
         p->nnz_off = csr->nnz - csr->n;
         try {
-            st = analyze_levels_device(p, csr, o.device, o.values);
+            st = analyze_levels_device(p, csr, o.device, o.values, p->reversed);
         } catch (const std::bad_alloc &) {
             st = fail(SPTRSV_ERR_OOM, "host allocation failed during analysis");
         }

@@ -246,6 +246,7 @@ __global__ void k_row_counts(const int32_t *rp, const int32_t *perm, int32_t n, 
 __global__ void k_set(int32_t *p, const AnaCtl *c) { *p = c->total; }
 
 struct LayoutOut {
+    int32_t flip;                   // 0, or n - 1 for a factor analysed with its ids reversed
     int32_t *col;
     double *val, *dinv;
     float *hi, *lo, *dhi, *dlo, *dinv32, *s32;
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_layout(int32_t n, const int32_t *r
         for (int32_t j = lane; j < last - lo; j += 32) {
             const double a = val[lo + j];
             const double s = __dmul_rn(a, dinv);
-            o.col[dst + j] = col[lo + j];
+            o.col[dst + j] = o.flip ? o.flip - col[lo + j] : col[lo + j];
             if (o.val) o.val[dst + j] = s;
             if (o.hi) {
                 const float h = __double2float_rn(a);
@@ -296,6 +297,12 @@ __global__ void __launch_bounds__(kThreads) k_layout(int32_t n, const int32_t *r
         atomicMax(&c->lnorm_bits, norm_bits);
         atomicMax(&c->max_row_off, widest);
     }
+}
+
+// Device row -> row of the caller's numbering (ids reversed for UPPER / LOWER_TRANSPOSED).
+__global__ void k_perm_out(const int32_t *perm, int32_t n, int32_t flip, int32_t *out) {
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < n; r += int64_t(gridDim.x) * blockDim.x)
+        out[r] = flip ? flip - perm[r] : perm[r];
 }
 
 __global__ void k_phase_ent(const int32_t *start, int32_t count, const int32_t *drp, int32_t *pent) {
@@ -361,7 +368,7 @@ struct SetDevice {
 
 }  // namespace
 
-int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values) {
+int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values, bool reversed) {
     SetDevice guard(device);
     HostSchedule &h = p->h;
     DeviceBuffers &d = p->d;
@@ -436,7 +443,8 @@ int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32
     k_row_counts<<<std::max(1, std::min(ntiles * kItems, 4096)), kThreads>>>(g_rp, perm, n, d.rp);
     if ((st = scan(d.rp, d.rp, n, tsum, c))) return st;
     k_set<<<1, 1>>>(d.rp + n, c);
-    LayoutOut o{d.col, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int32_t flip = reversed ? n - 1 : 0;
+    LayoutOut o{flip, d.col, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (values & SPTRSV_VALUES_F64) {
         if ((st = alloc_zeroed(&d.val, size_t(nnz_off), &bytes)) || (st = alloc_zeroed(&d.dinv, size_t(n), &bytes)))
             return st;
@@ -459,7 +467,8 @@ int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32
     k_layout<<<std::max(1, std::min((n + 7) / 8, sms * 8)), kThreads>>>(n, g_rp, g_col, g_val, perm, d.rp, o, c);
     k_phase_ent<<<std::max(1, std::min((S + 1 + 255) / 256, 1024)), 256>>>(start, S + 1, d.rp, d.phase_ent);
     ANA_TRY(cudaGetLastError());
-    ANA_TRY(cudaMemcpy(d.perm, perm, size_t(n) * sizeof(int32_t), cudaMemcpyDeviceToDevice));
+    k_perm_out<<<std::max(1, std::min(ntiles * kItems, 4096)), kThreads>>>(perm, n, flip, d.perm);
+    ANA_TRY(cudaGetLastError());
     ANA_TRY(cudaMemcpy(d.phase_row, start, (size_t(S) + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice));
     // host side of the plan: the schedule arrays and the per-wavefront tables
     h.level.resize(n);

@@ -139,8 +139,10 @@ int lower_factor(const sptrsv_csr *csr, int32_t triangle, std::vector<int32_t> &
 // Smallest safe shared-memory x ring of a one-block walk (0: none), as build_schedule sets it.
 int32_t ring_rows_of(const sptrsv_csr *A, const HostSchedule &h);
 // analyze_gpu.cu: the wavefront schedule, its Sec. 5 order and the device layout
-// computed on `device` from the caller's lower CSR (validated); fills p->h and p->d.
-int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values);
+// computed on `device` from the analysed lower CSR (validated); fills p->h and p->d.
+// reversed: A is L' with ids i' = n-1-i (UPPER, LOWER_TRANSPOSED); the device
+// column ids and permutation are written in the caller's numbering.
+int analyze_levels_device(sptrsv_plan *p, const sptrsv_csr *A, int device, int32_t values, bool reversed);
 // analyze_gpu.cu: the block-local layout's values gathered on the device from the
 // device-order arrays (entry q <- src[q], row t <- rsrc[t]); allocates l_val/l_dinv
 // and/or l_s32/l_dinv32 as the plan holds FP64 and/or FP32 values.
