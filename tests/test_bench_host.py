@@ -79,3 +79,26 @@ def test_reference_arm_silent_on_other_ranks():
                         "lap2d_64_f64", "--steps", "1", "--warmup", "1"], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("name", ["random_1m_f64", "random_1m_upper_f64", "lap2d_64_f64", "er_100k_f64",
+                                  "nb_100k_f64", "lap3d_160_f64"])
+def test_bench_workloads_are_valid_systems(name):
+    # every single-factor workload hands the solver a valid factor of its triangle and a
+    # right-hand side that is exactly A x* (the oracle's SpMV), with the sizes the line reports
+    import numpy as np
+    import bench
+    import oracle
+    spec = bench.WORKLOADS[name]
+    A, xs, b = spec["make"]()
+    if spec.get("triangle", "lower") == "upper":
+        oracle.validate_upper(A)
+    else:
+        oracle.validate(A)
+    assert xs.shape == b.shape == (A.n, spec["nrhs"])
+    r = oracle.spmv(A, xs) - b
+    assert np.max(np.abs(r)) <= 1e-12 * max(1.0, float(np.max(np.abs(b))))
+    if name == "random_1m_f64":
+        assert (A.n, A.nnz) == (1_000_000, 6_999_979)
+    if name == "lap3d_160_f64":
+        assert (A.n, A.nnz) == (4_096_000, 16_307_200)
