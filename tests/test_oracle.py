@@ -449,6 +449,21 @@ def test_funnel_hand_examples():
     assert part.tolist() == [0, 0, 1, 1] and roots == [1, 3]
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_funnel_single_sink_collapses_without_the_cap(seed):
+    # Sec. 4.2: without the size constraint a DAG with a single sink coarsens to one vertex
+    rng = np.random.default_rng(1500 + seed)
+    n = int(rng.integers(2, 60))
+    A = W.erdos_renyi_lower(n - 1, float(rng.uniform(0.02, 0.3)), seed)
+    parents = [A.col[A.rowptr[i]:A.rowptr[i + 1] - 1].tolist() for i in range(n - 1)]
+    has_child = set(u for p in parents for u in p)
+    parents.append([v for v in range(n - 1) if v not in has_child])      # every sink -> vertex n-1
+    part, roots = oracle.funnel_parts(n, parents, [1] * n, float("inf"))
+    assert roots == [n - 1] and not part.any()
+    part, roots = oracle.funnel_parts(n, parents, [1] * n, 3)            # the cap splits it again
+    assert len(roots) >= (n + 2) // 3
+
+
 @pytest.mark.parametrize("seed", range(25))
 def test_funnel_parts_are_in_funnels_and_coarsening_is_acyclic(seed):
     rng = np.random.default_rng(1300 + seed)
