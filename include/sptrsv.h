@@ -183,6 +183,12 @@ int sptrsv_plan_stats(const sptrsv_plan *plan, sptrsv_stats *out);
 int sptrsv_plan_export(const sptrsv_plan *plan, int32_t *level, int32_t *sigma, int32_t *pi,
                        int32_t *perm);
 
+/* Funnel plans (coarsen = FUNNEL): the part of every row, n int32 in the caller's
+ * numbering; parts are numbered 0..coarse_vertices-1.  For inspection and tests
+ * (Sec. 4: every part is an in-funnel of the triangle-reduced DAG).  Errors: ARG
+ * (NULL, or a plan not coarsened in this process, e.g. loaded from a file). */
+int sptrsv_plan_export_parts(const sptrsv_plan *plan, int32_t *part);
+
 /* ------------------------------------------------------- saved plans */
 /* Write an analysed plan to `path` so that another process can rebuild it with
  * sptrsv_plan_load without running the scheduler again: the file holds the

@@ -127,6 +127,7 @@ def lib():
             "sptrsv_plan_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
             "sptrsv_plan_export": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "sptrsv_local_partition": (ctypes.c_int, [ctypes.POINTER(CSRStruct), i32, i32, vp, vp]),
+            "sptrsv_plan_export_parts": (ctypes.c_int, [vp, vp]),
             "sptrsv_plan_save": (ctypes.c_int, [vp, ctypes.POINTER(CSRStruct), ctypes.c_char_p]),
             "sptrsv_plan_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(AnalyzeOpts),
                                                 ctypes.POINTER(vp)]),
@@ -265,6 +266,12 @@ class Plan:
         self.n = int(A.n)
         self.device = int(device)
         del self._rowptr, self._col, self._val       # analyze copied what it needs
+
+    def funnel_parts(self) -> np.ndarray:
+        """The Funnel part of every row (``sptrsv_plan_export_parts``)."""
+        part = np.empty(self.n, dtype=np.int32)
+        _check(lib().sptrsv_plan_export_parts(self.handle, _ptr(part)))
+        return part
 
     def save(self, A, path):
         """Write this plan and the factor ``A`` (the one it was analysed from, in the

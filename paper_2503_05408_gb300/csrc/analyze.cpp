@@ -395,7 +395,7 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
         if (o.coarsen == SPTRSV_COARSEN_FUNNEL)
             h.S = funnel_growlocal(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept,
                                    o.coarsen_max_weight > 0.0 ? o.coarsen_max_weight : 500.0, h.sigma.data(),
-                                   h.pi.data(), &h.coarse_vertices);
+                                   h.pi.data(), &h.coarse_vertices, &h.coarse_part);
         else
             h.S = growlocal_blocks(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept, h.sched_blocks,
                                    o.sched_threads, h.sigma.data(), h.pi.data());
@@ -667,6 +667,20 @@ int sptrsv_plan_export(const sptrsv_plan *p, int32_t *level, int32_t *sigma, int
         if (sigma) sigma[i] = p->h.sigma[size_t(n - 1 - i)];
         if (pi) pi[i] = p->h.pi[size_t(n - 1 - i)];
         if (perm) perm[i] = n - 1 - p->h.perm[size_t(i)];
+    }
+    return SPTRSV_OK;
+}
+
+int sptrsv_plan_export_parts(const sptrsv_plan *p, int32_t *part) {
+    if (!p || !part) return fail(SPTRSV_ERR_ARG, "NULL argument");
+    const int32_t n = p->h.n;
+    if (p->h.coarse_part.size() != size_t(n))
+        return fail(SPTRSV_ERR_ARG, "the plan was not scheduled on a Funnel-coarsened DAG in this process");
+    const int32_t m = p->h.coarse_vertices;
+    for (int32_t i = 0; i < n; ++i) {
+        // caller's numbering; for a reversed plan row i is row n-1-i of L', whose parts
+        // are renumbered so that part ids still increase with their root's caller id
+        part[i] = p->reversed ? m - 1 - p->h.coarse_part[size_t(n - 1 - i)] : p->h.coarse_part[size_t(i)];
     }
     return SPTRSV_OK;
 }

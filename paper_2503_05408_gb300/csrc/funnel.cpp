@@ -29,7 +29,7 @@ namespace sptrsv {
 
 int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k, double alpha0,
                          double growth, double L, double accept, double max_weight, int32_t *sigma, int32_t *pi,
-                         int32_t *parts) {
+                         int32_t *parts, std::vector<int32_t> *part_of) {
     *parts = 0;
     if (n == 0) return 0;
     // 1. triangle reduction: kept parents in CSR (kp, kc), ascending per row
@@ -51,7 +51,7 @@ int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, i
         }
     }
     // 2. in-funnel parts
-    std::vector<int32_t> outdeg(n, 0), count(n, 0), part(n, -1), roots, touched, members;
+    std::vector<int32_t> outdeg(n, 0), count(n, 0), part(n, -1), roots, touched;
     for (int32_t c : kc) outdeg[c]++;
     std::vector<int64_t> weight(n);
     for (int32_t v = 0; v < n; ++v) weight[v] = rowptr[v + 1] - rowptr[v];
@@ -107,6 +107,7 @@ int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, i
         pi[v] = cpi[part[v]];
     }
     *parts = m;
+    if (part_of) part_of->swap(part);
     return S;
 }
 

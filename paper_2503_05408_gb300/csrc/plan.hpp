@@ -33,6 +33,7 @@ struct HostSchedule {
     int32_t S = 0;
     int32_t sched_blocks = 1;        // diagonal blocks GrowLocal was run on (Sec. 3.1)
     int32_t coarse_vertices = 0;     // vertices of the scheduled DAG (Funnel parts, else n)
+    std::vector<int32_t> coarse_part; // Funnel plans: the part of every row (analysed numbering)
     double schedule_ms = 0.0;        // host wall time of the superstep schedule alone
     // block-local executor partition, once built (or read from a saved plan):
     // loc_blk[v] = block of row v, loc_lidx[v] = its position in the block's list
@@ -162,10 +163,11 @@ int32_t growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col,
                            double alpha0, double growth, double L, double accept, int32_t *sigma, int32_t *pi);
 // funnel.cpp: Funnel + GrowLocal (Sec. 4): triangle transitive reduction, in-funnel
 // coarsening with parts of weight <= max_weight, GrowLocal on the coarsened DAG,
-// each row taking its part's superstep and core.  *parts = coarsened vertices.
+// each row taking its part's superstep and core.  *parts = coarsened vertices;
+// part_of (optional) receives every row's part, parts numbered by root id.
 int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k, double alpha0,
                          double growth, double L, double accept, double max_weight, int32_t *sigma, int32_t *pi,
-                         int32_t *parts);
+                         int32_t *parts, std::vector<int32_t> *part_of = nullptr);
 // Block-parallel GrowLocal (Sec. 3.1): rows cut into `blocks` diagonal blocks of
 // floor(b n / blocks) .. floor((b+1) n / blocks) - 1, each block's sub-DAG
 // scheduled on one of `threads` host threads (0: one per hardware thread, at

@@ -395,3 +395,24 @@ def test_new_schedules_on_degenerate_factors(L, kw):
     else:
         s, pi, S = oracle.growlocal_blocks(two, 4, kw["sched_blocks"])
     assert ex.sigma.tolist() == s.tolist() and ex.pi.tolist() == pi.tolist()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("max_weight", [5.0, 500.0])
+def test_funnel_parts_bit_exact(L, name, max_weight):
+    # the library's coarsening itself, not only the schedule, equals the oracle's
+    A = CASES[name]()
+    p = _host_plan(A, mode="growlocal", k=8, coarsen="funnel", coarsen_max_weight=max_weight)
+    _, _, _, part = oracle.funnel_growlocal(A, 8, max_weight=max_weight)
+    assert np.array_equal(p.funnel_parts(), part)
+
+
+def test_funnel_parts_of_reversed_plans_group_the_same_rows(L):
+    L_ = W.narrow_band_lower(3000, 0.1, 10, 6)
+    U = W.transpose(L_)
+    pu = _host_plan(U, mode="growlocal", k=8, coarsen="funnel", triangle="upper").funnel_parts()
+    pt = _host_plan(L_, mode="growlocal", k=8, coarsen="funnel", triangle="lower_transposed").funnel_parts()
+    assert np.array_equal(pu, pt)
+    assert sorted(set(pu.tolist())) == list(range(int(pu.max()) + 1))
+    with pytest.raises(sp.SptrsvError):
+        _host_plan(L_, mode="growlocal", k=8).funnel_parts()        # not a Funnel plan
