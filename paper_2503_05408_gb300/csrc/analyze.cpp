@@ -394,8 +394,8 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
         h.coarse_vertices = n;
         if (o.coarsen == SPTRSV_COARSEN_FUNNEL)
             h.S = funnel_growlocal(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept,
-                                   o.coarsen_max_weight > 0.0 ? o.coarsen_max_weight : 500.0, h.sigma.data(),
-                                   h.pi.data(), &h.coarse_vertices, &h.coarse_part);
+                                   o.coarsen_max_weight > 0.0 ? o.coarsen_max_weight : 500.0, o.sched_threads,
+                                   h.sigma.data(), h.pi.data(), &h.coarse_vertices, &h.coarse_part);
         else
             h.S = growlocal_blocks(n, A->rowptr, A->col, o.k, o.alpha0, o.growth, o.L, o.accept, h.sched_blocks,
                                    o.sched_threads, h.sigma.data(), h.pi.data());

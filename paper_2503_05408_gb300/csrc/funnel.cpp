@@ -16,39 +16,83 @@
 //     order: only a part's root has edges leaving the part), a part weighing its
 //     rows' entries, one edge per pair of parts joined by a kept edge.  Every
 //     row takes its part's superstep and core.
-// Work O(sum deg^2) for step 1, O(|V| + |E|) for step 2 (Sec. 4.2).
+// Work O(sum deg^2) for step 1 (rows split over host threads), O(|V| + |E|) for
+// step 2 (Sec. 4.2).
 #include <algorithm>
 #include <cstdint>
+#include <exception>
 #include <queue>
-#include <utility>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "plan.hpp"
 
 namespace sptrsv {
 
+namespace {
+
+// Kept parents of rows [r0, r1): every parent u of w except those with u -> v -> w
+// for another parent v.  mark[] (n entries, this thread's) holds w for a parent
+// of w and -(w + 2) once that parent is found to be the long side of a triangle.
+void reduce_rows(int32_t r0, int32_t r1, const int32_t *rowptr, const int32_t *col, std::vector<int32_t> &mark,
+                 std::vector<int32_t> &kept, int32_t *kept_count) {
+    for (int32_t w = r0; w < r1; ++w) {
+        const int32_t lo = rowptr[w], last = rowptr[w + 1] - 1;
+        for (int32_t q = lo; q < last; ++q) mark[col[q]] = w;
+        for (int32_t q = lo; q < last; ++q) {
+            const int32_t v = col[q];
+            for (int32_t t = rowptr[v]; t < rowptr[v + 1] - 1; ++t)
+                if (mark[col[t]] == w) mark[col[t]] = -(w + 2);             // col[t] -> v -> w
+        }
+        int32_t c = 0;
+        for (int32_t q = lo; q < last; ++q)
+            if (mark[col[q]] == w) {
+                kept.push_back(col[q]);
+                ++c;
+            }
+        kept_count[w] = c;
+    }
+}
+
+}  // namespace
+
 int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k, double alpha0,
-                         double growth, double L, double accept, double max_weight, int32_t *sigma, int32_t *pi,
-                         int32_t *parts, std::vector<int32_t> *part_of) {
+                         double growth, double L, double accept, double max_weight, int32_t threads, int32_t *sigma,
+                         int32_t *pi, int32_t *parts, std::vector<int32_t> *part_of) {
     *parts = 0;
     if (n == 0) return 0;
-    // 1. triangle reduction: kept parents in CSR (kp, kc), ascending per row
+    // 1. triangle reduction, rows split over host threads: kept parents in CSR (kp, kc)
     std::vector<int32_t> kp(size_t(n) + 1, 0), kc;
-    kc.reserve(size_t(rowptr[n] - n));
     {
-        std::vector<int32_t> is_parent(n, -1), is_long(n, -1);
-        for (int32_t w = 0; w < n; ++w) {
-            const int32_t lo = rowptr[w], last = rowptr[w + 1] - 1;
-            for (int32_t q = lo; q < last; ++q) is_parent[col[q]] = w;
-            for (int32_t q = lo; q < last; ++q) {
-                const int32_t v = col[q];
-                for (int32_t t = rowptr[v]; t < rowptr[v + 1] - 1; ++t)
-                    if (is_parent[col[t]] == w) is_long[col[t]] = w;     // col[t] -> v -> w
+        // a thread keeps one n-entry mark array: at most 1 GiB of them in all
+        int32_t T = threads > 0 ? threads : int32_t(std::thread::hardware_concurrency());
+        T = std::max(1, std::min({T, std::max(1, n / 16384), int32_t(std::max<int64_t>(1, (int64_t(1) << 28) / n))}));
+        std::vector<std::vector<int32_t>> chunk(static_cast<size_t>(T));
+        std::vector<std::exception_ptr> err(static_cast<size_t>(T));
+        auto work = [&](int32_t t) {
+            try {
+                std::vector<int32_t> mark(static_cast<size_t>(n), -1);
+                reduce_rows(int32_t(int64_t(t) * n / T), int32_t(int64_t(t + 1) * n / T), rowptr, col, mark,
+                            chunk[t], kp.data() + 1);
+            } catch (...) {
+                err[t] = std::current_exception();
             }
-            for (int32_t q = lo; q < last; ++q)
-                if (is_long[col[q]] != w) kc.push_back(col[q]);
-            kp[w + 1] = int32_t(kc.size());
+        };
+        std::vector<std::thread> pool;
+        int32_t started = 1;
+        try {
+            for (; started < T; ++started) pool.emplace_back(work, started);
+        } catch (const std::system_error &) {
         }
+        work(0);
+        for (int32_t t = started; t < T; ++t) work(t);
+        for (auto &th : pool) th.join();
+        for (auto &e : err)
+            if (e) std::rethrow_exception(e);
+        for (int32_t w = 0; w < n; ++w) kp[w + 1] += kp[w];
+        kc.reserve(size_t(kp[n]));
+        for (auto &c : chunk) kc.insert(kc.end(), c.begin(), c.end());
     }
     // 2. in-funnel parts
     std::vector<int32_t> outdeg(n, 0), count(n, 0), part(n, -1), roots, touched;
@@ -82,18 +126,26 @@ int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, i
     // roots were found in decreasing id order: part index by increasing root
     const int32_t m = int32_t(roots.size());
     for (int32_t v = 0; v < n; ++v) part[v] = m - 1 - part[v];
-    // 3. coarsened DAG in CSR (parents ascending, diagonal last) and its weights
-    std::vector<std::pair<int32_t, int32_t>> e;                         // (child part, parent part)
+    // 3. coarsened DAG in CSR (parents ascending and unique, diagonal last) and its
+    //    weights: the kept edges between parts, bucketed by the child's part
+    std::vector<int64_t> cstart(size_t(m) + 1, 0);
     for (int32_t w = 0; w < n; ++w)
         for (int32_t q = kp[w]; q < kp[w + 1]; ++q)
-            if (part[kc[q]] != part[w]) e.push_back({part[w], part[kc[q]]});
-    std::sort(e.begin(), e.end());
-    e.erase(std::unique(e.begin(), e.end()), e.end());
+            if (part[kc[q]] != part[w]) cstart[size_t(part[w]) + 1]++;
+    for (int32_t i = 0; i < m; ++i) cstart[i + 1] += cstart[i];
+    std::vector<int32_t> cpar(static_cast<size_t>(cstart[m]));
+    {
+        std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+        for (int32_t w = 0; w < n; ++w)
+            for (int32_t q = kp[w]; q < kp[w + 1]; ++q)
+                if (part[kc[q]] != part[w]) cpar[size_t(fill[part[w]]++)] = part[kc[q]];
+    }
     std::vector<int32_t> crp(size_t(m) + 1, 0), ccol;
-    ccol.reserve(e.size() + size_t(m));
-    size_t t = 0;
+    ccol.reserve(cpar.size() + size_t(m));
     for (int32_t i = 0; i < m; ++i) {
-        for (; t < e.size() && e[t].first == i; ++t) ccol.push_back(e[t].second);
+        auto b = cpar.begin() + cstart[i], e = cpar.begin() + cstart[i + 1];
+        std::sort(b, e);
+        ccol.insert(ccol.end(), b, std::unique(b, e));
         ccol.push_back(i);
         crp[i + 1] = int32_t(ccol.size());
     }

@@ -165,9 +165,10 @@ int32_t growlocal_weighted(int32_t n, const int32_t *rowptr, const int32_t *col,
 // coarsening with parts of weight <= max_weight, GrowLocal on the coarsened DAG,
 // each row taking its part's superstep and core.  *parts = coarsened vertices;
 // part_of (optional) receives every row's part, parts numbered by root id.
+// threads: host threads of the triangle reduction (0: one per hardware thread).
 int32_t funnel_growlocal(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t k, double alpha0,
-                         double growth, double L, double accept, double max_weight, int32_t *sigma, int32_t *pi,
-                         int32_t *parts, std::vector<int32_t> *part_of = nullptr);
+                         double growth, double L, double accept, double max_weight, int32_t threads, int32_t *sigma,
+                         int32_t *pi, int32_t *parts, std::vector<int32_t> *part_of = nullptr);
 // Block-parallel GrowLocal (Sec. 3.1): rows cut into `blocks` diagonal blocks of
 // floor(b n / blocks) .. floor((b+1) n / blocks) - 1, each block's sub-DAG
 // scheduled on one of `threads` host threads (0: one per hardware thread, at
