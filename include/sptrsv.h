@@ -110,8 +110,9 @@ typedef struct {
                           the block schedules are concatenated: a vertex of block b gets
                           its block superstep plus the supersteps of blocks 0..b-1.  The
                           result does not depend on sched_threads.                        */
-    int32_t sched_threads; /* host threads for the blocks; 0 = one per hardware thread,
-                          never more than B                                               */
+    int32_t sched_threads; /* host threads for the schedule blocks (never more than B) and for
+                          Funnel's triangle reduction; 0 = one per hardware thread.  The
+                          schedule never depends on it.                                    */
     int32_t coarsen;   /* GROWLOCAL only, SPTRSV_COARSEN_*: FUNNEL schedules the DAG coarsened
                           by in-funnels (Sec. 4, Algorithm 4.1) after dropping the long edge of
                           every triangle u->v->w; each row takes its part's superstep and core.

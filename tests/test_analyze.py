@@ -416,3 +416,15 @@ def test_funnel_parts_of_reversed_plans_group_the_same_rows(L):
     assert sorted(set(pu.tolist())) == list(range(int(pu.max()) + 1))
     with pytest.raises(sp.SptrsvError):
         _host_plan(L_, mode="growlocal", k=8).funnel_parts()        # not a Funnel plan
+
+
+def test_funnel_independent_of_threads(L):
+    A = W.erdos_renyi_lower(60_000, 5e-4, 9)
+    ref = None
+    for threads in (1, 2, 3, 0):
+        p = _host_plan(A, mode="growlocal", k=64, coarsen="funnel", sched_threads=threads)
+        got = (p.export().sigma, p.export().pi, p.funnel_parts())
+        if ref is None:
+            ref = got
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
