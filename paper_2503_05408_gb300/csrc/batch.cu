@@ -576,7 +576,7 @@ int sptrsv_batch_run(sptrsv_batch *B, const void *const *b, void *const *x, cons
     if (!st) st = build_graph(B);
     if (!st) {
         fill_vectors(B, b, x, ld);
-        // pageable source: the driver stages it, so the host copy may change right after the call
+        // pageable source: the CUDA driver stages it, so the host copy may change right after the call
         cudaError_t e = cudaMemcpyAsync(B->d_items, B->items.data(), B->items.size() * sizeof(BatchItem),
                                         cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, s);
