@@ -159,7 +159,9 @@ int sptrsv_plan_load(const char *path, const sptrsv_analyze_opts *opts, sptrsv_p
     if (std::memcmp(hd.magic, kMagic, 8) != 0) return fail(SPTRSV_ERR_ARG, "not a saved plan");
     if (hd.version != kVersion) return fail(SPTRSV_ERR_ARG, "saved plan of another format version");
     if (hd.order != kOrder) return fail(SPTRSV_ERR_ARG, "saved plan of another byte order");
-    if (hd.n < 0 || hd.nnz < hd.n || hd.nnz > (int64_t(1) << 31) - 1 || hd.loc_nb < 0 || hd.k < 1 || hd.S < 0)
+    if (hd.n < 0 || hd.nnz < hd.n || hd.nnz > (int64_t(1) << 31) - 1 || hd.loc_nb < 0 || hd.k < 1 ||
+        hd.k > (1 << 20) || hd.S < 0 || hd.S > hd.n || hd.coarse < 0 || hd.coarse > hd.n ||
+        (hd.mode != SPTRSV_SCHED_LEVELS && hd.mode != SPTRSV_SCHED_GROWLOCAL))
         return fail(SPTRSV_ERR_ARG, "saved plan: bad header");
     const size_t n = size_t(hd.n), nnz = size_t(hd.nnz);
     {   // the size the header promises, before allocating anything

@@ -200,3 +200,15 @@ def test_load_refuses_factor_damage_with_valid_checksum(tmp_path):
     a, b = struct.unpack_from("<ii", d, q)
     struct.pack_into("<ii", d, q, b, a)
     _refused(tmp_path, _fix_checksum(d), sp.ERR_UNSORTED_OR_DUP)
+
+
+def test_load_refuses_out_of_range_header_fields(tmp_path):
+    A, path, data = _saved(tmp_path)
+    n = A.n
+    for off, value in ((36, (1 << 20) + 1),      # k
+                       (40, n + 1),              # supersteps
+                       (32, 7),                  # mode
+                       (52, n + 1)):             # coarsened vertices
+        d = bytearray(data)
+        struct.pack_into("<i", d, off, value)
+        _refused(tmp_path, d, sp.ERR_ARG)
