@@ -428,3 +428,40 @@ def test_funnel_independent_of_threads(L):
             ref = got
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)
+
+
+def _reversed_lower(U):
+    """L' with rows and columns numbered backwards: row i' of L' is row n-1-i' of U."""
+    n = U.n
+    cols, vals, rp = [], [], [0]
+    for i2 in range(n):
+        i = n - 1 - i2
+        lo, hi = U.rowptr[i], U.rowptr[i + 1]
+        cols.append((n - 1 - U.col[lo:hi])[::-1])
+        vals.append(U.val[lo:hi][::-1])
+        rp.append(rp[-1] + hi - lo)
+    return W.CSR(n, np.array(rp, np.int32), np.concatenate(cols).astype(np.int32), np.concatenate(vals), "rev")
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("sched", ["funnel", "blocks"])
+def test_reversed_plans_schedule_the_reversed_factor(L, seed, sched):
+    # U x = b and L^T x = b are scheduled as L' (ids reversed): in the caller's numbering
+    # the library's schedule is the oracle's schedule of L' read backwards
+    rng = np.random.default_rng(8800 + seed)
+    n = int(rng.integers(2, 900))
+    Lo = (W.narrow_band_lower(n, float(rng.uniform(0.05, 0.5)), float(rng.uniform(2, 20)), seed) if seed % 2
+          else W.erdos_renyi_lower(n, float(rng.uniform(2e-3, 0.03)), seed))
+    U = W.transpose(Lo)
+    Lr = _reversed_lower(U)
+    oracle.validate(Lr)
+    k = int(rng.integers(1, 30))
+    if sched == "funnel":
+        kw = dict(coarsen="funnel")
+        s, pi = oracle.funnel_growlocal(Lr, k)[:2]
+    else:
+        kw = dict(sched_blocks=int(rng.integers(2, 9)))
+        s, pi = oracle.growlocal_blocks(Lr, k, kw["sched_blocks"])[:2]
+    for tri, A in (("upper", U), ("lower_transposed", Lo)):
+        ex = _host_plan(A, mode="growlocal", k=k, triangle=tri, **kw).export()
+        assert np.array_equal(ex.sigma, s[::-1]) and np.array_equal(ex.pi, pi[::-1])
