@@ -283,7 +283,10 @@ typedef struct {
                             partial sum reduced, so the lane that receives the last parent
                             publishes after one FMA (best when a row's parents finish at
                             different times); OFF: reduce once all parents are in (best when
-                            they arrive together, e.g. stencils).  AUTO = tuned value, else ON */
+                            they arrive together, e.g. stencils).  AUTO = tuned value, else ON.
+                            Polled sums follow the parents' arrival order: with ON, or with
+                            several entries per lane, the last bits of x may differ between
+                            runs (always within the solve's accuracy)                          */
 } sptrsv_solve_opts;
 enum { SPTRSV_EAGER_AUTO = 0, SPTRSV_EAGER_ON = 1, SPTRSV_EAGER_OFF = 2 };
 
