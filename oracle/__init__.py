@@ -469,10 +469,17 @@ def permute(A, perm):
 
 
 def rel_error(x, xref) -> float:
-    """Normwise relative error max_i |x_i - xref_i| / max_i |xref_i|, worst column."""
-    x = np.asarray(x, dtype=np.float64).reshape(np.shape(xref)[0], -1)
-    xr = np.asarray(xref, dtype=np.float64).reshape(np.shape(xref)[0], -1)
+    """Normwise relative error max_i |x_i - xref_i| / max_i |xref_i| per right-hand-side
+    column, worst column returned (the error metric of the parity checks).  A column whose
+    reference is all zeros reports its absolute error; an empty system has error 0."""
+    xr = np.asarray(xref, dtype=np.float64)
+    n = xr.shape[0]
+    cols = xr.size // n if n else (xr.shape[1] if xr.ndim > 1 else 1)
+    xr = xr.reshape(n, cols)
+    x = np.asarray(x, dtype=np.float64).reshape(n, cols)
+    if x.size == 0:
+        return 0.0                     # no entries: nothing differs
     num = np.max(np.abs(x - xr), axis=0)
     den = np.max(np.abs(xr), axis=0)
     den = np.where(den == 0, 1.0, den)
-    return float(np.max(num / den)) if num.size else 0.0
+    return float(np.max(num / den))

@@ -627,3 +627,33 @@ def test_validate_upper_rejects_bad_inputs():
         oracle.validate_upper(bad)
     with pytest.raises(oracle.InvalidFactor):
         oracle.validate_upper(W.laplace2d_lower(64, 8))       # lower, diagonal last
+
+
+# ---------------------------------------------------------------- error metric
+def test_rel_error_hand_values():
+    """The normwise relative error every parity test goes through (reading iv of
+    the error metric: max_i |x_i - xref_i| / max_i |xref_i| per right-hand-side
+    column, worst column reported), on values worked out by hand."""
+    xref = np.array([[1.0, 10.0], [2.5, 20.0], [3.0, 28.0]])
+    x = np.array([[1.0, 10.0], [2.0, 20.0], [3.0, 30.0]])
+    # column 0: max |diff| = 0.5, max |xref| = 3  -> 1/6
+    # column 1: max |diff| = 2.0, max |xref| = 28 -> 1/14
+    assert oracle.rel_error(x, xref) == pytest.approx(1.0 / 6.0, rel=1e-15)
+    # per-column denominators: one shared over both columns (28) would give 1/14
+    assert oracle.rel_error(x[:, 1:], xref[:, 1:]) == pytest.approx(1.0 / 14.0, rel=1e-15)
+    # the worst column decides, whichever position it holds
+    assert oracle.rel_error(x[:, ::-1], xref[:, ::-1]) == pytest.approx(1.0 / 6.0, rel=1e-15)
+    # absolute values in numerator and denominator: [1, 2, -4] vs [1, 2, -5] -> 1/5
+    assert oracle.rel_error(np.array([1.0, 2.0, -4.0]), np.array([1.0, 2.0, -5.0])) == pytest.approx(0.2)
+    # the reference is the second argument: |2 - 1| / 1 against |1 - 2| / 2
+    assert oracle.rel_error(np.array([2.0]), np.array([1.0])) == 1.0
+    assert oracle.rel_error(np.array([1.0]), np.array([2.0])) == 0.5
+    # a vector and an n x 1 block are the same single column (no broadcasting)
+    v, vr = np.array([1.0, 2.0, 4.0]), np.array([1.0, 2.5, 4.0])
+    assert oracle.rel_error(v, vr.reshape(3, 1)) == pytest.approx(0.125)
+    assert oracle.rel_error(v.reshape(3, 1), vr) == pytest.approx(0.125)
+    # a zero reference column falls back to the absolute error of that column
+    assert oracle.rel_error(np.array([[0.0, 1.0], [0.25, 1.0]]), np.array([[0.0, 1.0], [0.0, 1.0]])) == 0.25
+    # exact agreement and empty inputs
+    assert oracle.rel_error(xref, xref) == 0.0
+    assert oracle.rel_error(np.zeros((0, 2)), np.zeros((0, 2))) == 0.0
