@@ -28,7 +28,7 @@ namespace {
 constexpr int kCtlWords = 64;                              // 256 bytes of control words
 constexpr int32_t kMaxRows = SPTRSV_NOALLOC_MAX_ROWS;
 
-// [0] status, [2..3] flag waits (u64), [kCtlWords ...] one ready flag per row.
+// [0] status word, [1 .. kCtlWords) spare, [kCtlWords ...] one ready flag per row.
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kCtlWords + kMaxRows];
 
 struct DeviceSlot {
@@ -55,7 +55,6 @@ k_flags_csr_noalloc(int32_t n, int64_t nnz, const int32_t *__restrict__ rowptr, 
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long waits = 0;
     for (int r = gw; r < n; r += nw) {
         const int32_t beg = rowptr[r], end = rowptr[r + 1];
         // the factor is not validated on the host: check what would break memory safety
@@ -74,7 +73,6 @@ k_flags_csr_noalloc(int32_t n, int64_t nnz, const int32_t *__restrict__ rowptr, 
             }
             const uint32_t *f = flags + c;
             if (ld_acquire(f) != epoch) {
-                ++waits;
                 const long long t0 = gtimer();
                 unsigned spins = 0;
                 while (ld_acquire(f) != epoch) {
@@ -100,7 +98,6 @@ k_flags_csr_noalloc(int32_t n, int64_t nnz, const int32_t *__restrict__ rowptr, 
         }
         __syncwarp();
     }
-    if (waits) atomicAdd(reinterpret_cast<unsigned long long *>(ctl + 2), waits);
 }
 
 // Per-device set-up, run once with that device current: resolve the device
@@ -145,8 +142,10 @@ extern "C" int sptrsv_solve_csr_noalloc(int32_t n, int64_t nnz, const int32_t *r
     if (nnz < n || nnz > INT32_MAX) return fail(SPTRSV_ERR_ARG, "nnz must be in [n, 2^31)");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(SPTRSV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(SPTRSV_ERR_ARG, "sptrsv_solve_csr_noalloc: device index " + std::to_string(dev) +
+                                        " exceeds the " + std::to_string(kMaxDevices) + " devices it tracks");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint32_t *scratch;
     uint32_t epoch;

@@ -335,6 +335,24 @@ def test_full_size_3d_refine(nrhs):
     assert oracle.rel_error(x, xs) <= F64_TOL
 
 
+def test_full_size_3d_f64_r32():
+    # 160^3 stencil, 32 right-hand sides (column-major), plain FP64: the explicit
+    # polled and grid-barrier tiles and the launch shape the autotuner picks
+    A, xs, b = W.config_3d_160(nrhs=32)
+    xo = oracle.solve(A, b)
+    assert oracle.rel_error(xo, xs) < 1e-13
+    plan = sp.Plan(A, analyze_on_device=True)
+    for sync in ("flags", "grid"):
+        x, rep = solve_gpu(plan, b, sync=sync, rhs_tile=32)
+        assert rep["status"] == 0
+        assert oracle.rel_error(x, xo) <= F64_TOL
+    bd = to_dev(b)
+    xd = torch.empty_like(bd)
+    opts = plan.autotune(bd, xd, precision="f64")
+    x, rep = solve_gpu(plan, b, precision="f64", **opts)
+    assert oracle.rel_error(x, xo) <= F64_TOL
+
+
 def test_full_size_random_refine():
     A, xs, b = W.config_random_1m()
     xo = oracle.solve(A, b)
