@@ -104,6 +104,7 @@ def parse_args():
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--blocks-per-sm", type=int, default=None)
     ap.add_argument("--rhs-tile", type=int, default=None)
+    ap.add_argument("--partition", default=None, help="block-local executors: parents | ranges")
     ap.add_argument("--schedule", choices=["levels", "growlocal"], default="levels",
                     help="superstep schedule of the analysis (single-factor workloads)")
     ap.add_argument("--sched-blocks", type=int, default=0,
@@ -345,7 +346,7 @@ def run_ours(args):
     x = torch.empty_strided(b.shape, b.stride(), dtype=tdtype, device=b.device)
     precision = args.precision or spec.get("precision", "f64")
     opts = dict(sync=args.sync, lanes=args.lanes, threads=args.threads, blocks_per_sm=args.blocks_per_sm,
-                rhs_tile=args.rhs_tile)
+                rhs_tile=args.rhs_tile, partition=args.partition)
     opts = {k: v for k, v in opts.items() if v is not None}
     opts["precision"] = precision
     if "sync" not in opts:
@@ -441,14 +442,19 @@ def run_ours(args):
                    "sched_blocks": st["sched_blocks"], "schedule_ms": st["schedule_ms"],
                    "analysis": "device" if on_device else "host",
                    "sync": rep["sync_name"], "lanes": rep["lanes"], "grid": rep["grid"],
-                   "threads": rep["threads"]},
+                   "threads": rep["threads"], "partition": opts.get("partition")},
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(b_host.numel() * 8),
                 "d2h_bytes_per_step": int(x_host.numel() * 8)},
         # refinement: 8 residual + 7 sweep launches per solve at the default max_iters = 6
         "gpu_launches": args.steps * (1 if precision == "f64" else 15),
         "clocks": clk,
-        "sync_points_per_step": rep["barriers"] + rep["flag_waits"],
+        # fixed by the plan: grid barriers (barrier executors) or dependency edges whose parent
+        # is owned by another thread block (block-local executors, one global-memory hop each);
+        # beside it, the waits that actually had to spin in the last solve
+        "sync_points_per_step": rep["barriers"] if rep["cross_edges"] < 0 else rep["cross_edges"],
+        "sync_points": {"barriers": rep["barriers"], "cross_block_edges": rep["cross_edges"],
+                        "edges": rep["edges"], "spinning_waits": rep["flag_waits"]},
         "analyze_ms": analyze_s * 1e3,
         "precision": precision,
         "refine_sweeps": rep["sweeps"],
@@ -752,7 +758,8 @@ def run_serve_reference(args):
     return 0
 
 
-SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta", "cta_regs": "cta_regs", "local": "local"}
+SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta", "cta_regs": "cta_regs", "local": "local",
+            "chunks": "chunks", "waves": "waves"}
 
 
 def main():

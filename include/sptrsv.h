@@ -232,6 +232,12 @@ int sptrsv_plan_load(const char *path, const sptrsv_analyze_opts *opts, sptrsv_p
  * validation errors of sptrsv_analyze. */
 int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
                            int32_t *position);
+/* Host-only: the same for any partition kind (SPTRSV_PART_PARENTS, RANGES or GRID;
+ * GRID falls back to PARENTS on a factor without nested-stride structure), as the
+ * block-local executors build it.  Arguments and errors as sptrsv_local_partition,
+ * plus ARG for another kind. */
+int sptrsv_block_partition(const sptrsv_csr *A, int32_t kind, int32_t blocks, int32_t row_cap,
+                           int32_t *block_of_row, int32_t *position);
 
 /* Release a plan and its device memory (NULL is a no-op).  The caller must
  * ensure no enqueued solve still uses it. */
@@ -247,7 +253,7 @@ enum {
                                phase is staged into shared memory by TMA bulk copies ahead of
                                use when the plan's largest phase fits                       */
     SPTRSV_SYNC_CTA_REGS = 4, /* one thread block, register prefetch only (no staging)      */
-    SPTRSV_SYNC_LOCAL = 5   /* persistent grid, one block per SM (threads up to 1024); rows
+    SPTRSV_SYNC_LOCAL = 5,  /* persistent grid, one block per SM (threads up to 1024); rows
                                partitioned over the blocks so that most dependencies, above
                                all each row's last-finishing parent, stay inside one block
                                (Sec. 3's locality principle applied to SMs); a block keeps its
@@ -257,6 +263,33 @@ enum {
                                mode (synchronous: device-to-host copy, host pass, upload) and
                                kept in the plan.  ARG if nrhs > 1 or if the rows do not fit the
                                shared memory of the grid's blocks                            */
+    SPTRSV_SYNC_CHUNKS = 6, /* the block-local partition of SYNC_LOCAL executed one row per
+                               lane: each block's (wavefront, id) list is cut into chunks of
+                               up to 32 rows of one wavefront, a warp waits until every
+                               parent of its chunk has landed and then runs Eq. 2.1 for all
+                               of its rows at once (full-warp FP64 instructions; entries
+                               stored sliced, 32 lanes per entry slot).  A row's sum runs in a
+                               fixed order (parents of other blocks first, then its own block's,
+                               each in column order): the same bits every run.  One right-hand
+                               side, at most 512 threads per block; ARG as for SYNC_LOCAL    */
+    SPTRSV_SYNC_WAVES = 7   /* the chunks of SYNC_CHUNKS, but every block steps through its
+                               own wavefronts with one block barrier between them (the Sec.
+                               2.2 superstep at the scale of one SM): parents in the same
+                               block are read from shared memory untested, parents in other
+                               blocks are polled, their loads issued a wavefront ahead.
+                               Same results, limits and errors as SYNC_CHUNKS                */
+};
+enum {
+    SPTRSV_PART_AUTO = 0,    /* the partition the plan holds (saved, built or tuned), else PARENTS */
+    SPTRSV_PART_PARENTS = 1, /* rows follow their parents (see sptrsv_local_partition)          */
+    SPTRSV_PART_RANGES = 2,  /* contiguous ranges of row ids, n / blocks rows each: the natural
+                                order keeps a structured grid's neighbours together, and every
+                                dependency goes to the same or a later block                    */
+    SPTRSV_PART_GRID = 3     /* a factor whose off-diagonal offsets are dominated by nested
+                                strides 1 | s1 | s2 (a 3D grid in natural order, detected from
+                                the pattern) is cut into pencils along the fastest stride, tiled
+                                over the other two: the blocks' dependency graph is acyclic and a
+                                dependency path crosses few blocks.  Other factors: PARENTS     */
 };
 enum {
     SPTRSV_PREC_F64 = 0,         /* FP64 values and arithmetic (needs SPTRSV_VALUES_F64)    */
@@ -287,6 +320,9 @@ typedef struct {
                             Polled sums follow the parents' arrival order: with ON, or with
                             several entries per lane, the last bits of x may differ between
                             runs (always within the solve's accuracy)                          */
+    int32_t partition;   /* SYNC_LOCAL / SYNC_CHUNKS: SPTRSV_PART_*, the row -> thread block
+                            partition.  A plan keeps one partition; asking for another kind
+                            rebuilds it (synchronous host pass)                                 */
 } sptrsv_solve_opts;
 enum { SPTRSV_EAGER_AUTO = 0, SPTRSV_EAGER_ON = 1, SPTRSV_EAGER_OFF = 2 };
 
@@ -304,6 +340,10 @@ typedef struct {
     int32_t threads;       /* threads per block                                               */
     double berr;           /* refinement: last normwise backward error max|r| /
                               (||L||inf max|x| + max|b|) computed in FP64 (0 for a plain solve) */
+    int64_t cross_edges;   /* SYNC_LOCAL / SYNC_CHUNKS: dependency edges whose parent belongs to
+                              another thread block (each one global-memory hop; fixed by the
+                              partition); the other modes: -1                                  */
+    int64_t edges;         /* dependency edges of the factor (off-diagonal entries)            */
 } sptrsv_report;
 
 /* Solve L X = B for nrhs right-hand sides (Eq. 2.1 in the plan's schedule).

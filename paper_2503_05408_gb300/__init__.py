@@ -29,14 +29,17 @@ COARSEN_NONE, COARSEN_FUNNEL = 0, 1
 _COARSEN = {"none": COARSEN_NONE, "funnel": COARSEN_FUNNEL}
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
-SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL = 0, 1, 2, 3, 4, 5
+SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL, SYNC_CHUNKS, SYNC_WAVES = range(8)
+PART_AUTO, PART_PARENTS, PART_RANGES, PART_GRID = 0, 1, 2, 3
 PREC_F64, PREC_F32_REFINE = 0, 1
 
 SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta",
-              SYNC_CTA_REGS: "cta_regs", SYNC_LOCAL: "local"}
+              SYNC_CTA_REGS: "cta_regs", SYNC_LOCAL: "local", SYNC_CHUNKS: "chunks",
+              SYNC_WAVES: "waves"}
 _SYNC = {v: k for k, v in SYNC_NAMES.items()}
 _MODE = {"levels": SCHED_LEVELS, "growlocal": SCHED_GROWLOCAL}
 _PREC = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}
+_PART = {"auto": PART_AUTO, "parents": PART_PARENTS, "ranges": PART_RANGES, "grid": PART_GRID}
 
 
 class SptrsvError(RuntimeError):
@@ -74,14 +77,14 @@ class SolveOpts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("timeout_s", ctypes.c_double), ("rhs_tile", ctypes.c_int32),
-                ("eager_sum", ctypes.c_int32)]
+                ("eager_sum", ctypes.c_int32), ("partition", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("barriers", ctypes.c_int64),
                 ("flag_waits", ctypes.c_int64), ("dnorm", ctypes.c_double), ("sync", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("berr", ctypes.c_double)]
+                ("berr", ctypes.c_double), ("cross_edges", ctypes.c_int64), ("edges", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -127,6 +130,7 @@ def lib():
             "sptrsv_plan_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
             "sptrsv_plan_export": (ctypes.c_int, [vp, vp, vp, vp, vp]),
             "sptrsv_local_partition": (ctypes.c_int, [ctypes.POINTER(CSRStruct), i32, i32, vp, vp]),
+            "sptrsv_block_partition": (ctypes.c_int, [ctypes.POINTER(CSRStruct), i32, i32, i32, vp, vp]),
             "sptrsv_plan_export_parts": (ctypes.c_int, [vp, vp]),
             "sptrsv_plan_save": (ctypes.c_int, [vp, ctypes.POINTER(CSRStruct), ctypes.c_char_p]),
             "sptrsv_plan_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(AnalyzeOpts),
@@ -202,6 +206,8 @@ def solve_opts(**kw) -> SolveOpts:
             v = _SYNC[v]
         if key == "precision" and isinstance(v, str):
             v = _PREC[v]
+        if key == "partition" and isinstance(v, str):
+            v = _PART[v]
         setattr(o, key, v)
     return o
 
@@ -212,6 +218,21 @@ class ScheduleExport:
     sigma: np.ndarray
     pi: np.ndarray
     perm: np.ndarray
+
+
+def block_partition(A, blocks, kind="parents", row_cap=0):
+    """Host-only: (block of each row, position in its block's list) of the partition of
+    kind ``parents``, ``ranges`` or ``grid`` for ``blocks`` thread blocks
+    (``sptrsv_block_partition``)."""
+    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.col, dtype=np.int32)
+    val = np.ascontiguousarray(A.val, dtype=np.float64)
+    csr = CSRStruct(int(A.n), int(col.size), _ptr(rowptr), _ptr(col), _ptr(val))
+    blk = np.zeros(int(A.n), dtype=np.int32)
+    pos = np.zeros(int(A.n), dtype=np.int32)
+    k = _PART[kind] if isinstance(kind, str) else int(kind)
+    _check(lib().sptrsv_block_partition(ctypes.byref(csr), k, int(blocks), int(row_cap), _ptr(blk), _ptr(pos)))
+    return blk, pos
 
 
 def local_partition(A, blocks, row_cap=0):
@@ -328,7 +349,8 @@ class Plan:
                                      ctypes.byref(solve_opts(**base)), _stream_handle(stream),
                                      ctypes.byref(best), ctypes.byref(ms)))
         out = {"sync": best.sync, "lanes": best.lanes, "threads": best.threads,
-               "blocks_per_sm": best.blocks_per_sm, "rhs_tile": best.rhs_tile, "eager_sum": best.eager_sum}
+               "blocks_per_sm": best.blocks_per_sm, "rhs_tile": best.rhs_tile, "eager_sum": best.eager_sum,
+               "partition": best.partition}
         self.tuned_ms = ms.value
         return out
 

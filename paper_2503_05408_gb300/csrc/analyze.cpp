@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "plan.hpp"
@@ -257,7 +258,87 @@ bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<i
 }
 
 
-// A saved schedule is accepted only if the executors can run it: supersteps
+bool range_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                     std::vector<int32_t> &blk, std::vector<int32_t> &lidx, std::vector<int32_t> &load) {
+    if (nb < 1 || int64_t(row_cap) * nb < int64_t(n)) return false;
+    blk.assign(n, 0);
+    lidx.assign(n, 0);
+    load.assign(nb, 0);
+    for (int32_t v = 0; v < n; ++v) {
+        blk[v] = int32_t(int64_t(v) * nb / std::max<int32_t>(n, 1));
+        if (++load[blk[v]] > row_cap) return false;
+    }
+    // positions in (wavefront, id) order inside every block
+    std::vector<int32_t> lstart(size_t(nlevels) + 1, 0), ord(n);
+    for (int32_t v = 0; v < n; ++v) lstart[level[v] + 1]++;
+    for (int32_t l = 0; l < nlevels; ++l) lstart[l + 1] += lstart[l];
+    for (int32_t v = 0; v < n; ++v) ord[lstart[level[v]]++] = v;
+    std::vector<int32_t> fill(nb, 0);
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = ord[t];
+        lidx[v] = fill[blk[v]]++;
+    }
+    return true;
+}
+
+bool grid_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                    const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
+                    std::vector<int32_t> &lidx, std::vector<int32_t> &load) {
+    if (nb < 1 || n < 1 || int64_t(row_cap) * nb < int64_t(n)) return false;
+    // offsets v - c of the off-diagonal entries, on every 16th row
+    std::unordered_map<int64_t, int64_t> count;
+    int64_t sampled = 0;
+    for (int32_t v = 0; v < n; v += 16) {
+        ++sampled;
+        const int32_t dr = row_of[v];
+        for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q) count[int64_t(v) - col[q]]++;
+    }
+    std::vector<int64_t> dom;                        // offsets present in a quarter of the rows
+    for (const auto &e : count)
+        if (4 * e.second >= sampled) dom.push_back(e.first);
+    std::sort(dom.begin(), dom.end());
+    // nested strides 1 | s1 | s2: the largest three-term chain of dominant offsets
+    int64_t s1 = 0, s2 = 0;
+    if (dom.empty() || dom[0] != 1) return false;
+    for (size_t a = 1; a < dom.size(); ++a)
+        for (size_t b = a + 1; b < dom.size(); ++b)
+            if (dom[b] % dom[a] == 0 && dom[b] / dom[a] >= 2 && dom[a] >= 2 && dom[b] > s2) {
+                s1 = dom[a];
+                s2 = dom[b];
+            }
+    if (s2 == 0) return false;
+    const int64_t A = s2 / s1;                       // lines per plane
+    const int64_t B = (int64_t(n) + s2 - 1) / s2;    // planes
+    // tiles TA x TB <= nb, as many as possible, tile sides within a factor 3 of each other
+    int64_t TA = 0, TB = 0;
+    for (int64_t ta = 1; ta <= std::min<int64_t>(A, nb); ++ta) {
+        const int64_t tb = std::min<int64_t>(B, nb / ta);
+        const double side_a = double(A) / ta, side_b = double(B) / tb;
+        if (side_a > 3 * side_b || side_b > 3 * side_a) continue;
+        if (ta * tb > TA * TB || (ta * tb == TA * TB && std::abs(side_a - side_b) <
+                                  std::abs(double(A) / TA - double(B) / TB)))
+            TA = ta, TB = tb;
+    }
+    if (TA * TB < 2) return false;
+    blk.assign(n, 0);
+    load.assign(nb, 0);
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t a = (v / s1) % A, b = v / s2;
+        const int64_t ta = a * TA / A, tb = b * TB / B;
+        blk[v] = int32_t(tb * TA + ta);
+        if (++load[blk[v]] > row_cap) return false;
+    }
+    std::vector<int32_t> lstart(size_t(nlevels) + 1, 0), ord(n);
+    for (int32_t v = 0; v < n; ++v) lstart[level[v] + 1]++;
+    for (int32_t l = 0; l < nlevels; ++l) lstart[l + 1] += lstart[l];
+    for (int32_t v = 0; v < n; ++v) ord[lstart[level[v]]++] = v;
+    lidx.assign(n, 0);
+    std::vector<int32_t> fill(nb, 0);
+    for (int32_t t = 0; t < n; ++t) lidx[ord[t]] = fill[blk[ord[t]]]++;
+    return true;
+}
+
+// A saved schedule is accepted only if the executors can run it// A saved schedule is accepted only if the executors can run it: supersteps
 // 0..S-1 all used, cores in [0, k), every edge into a later superstep or inside
 // one core's block (Def. 2.1); a wavefront schedule must be the wavefronts.
 int check_given(const sptrsv_csr *A, const HostSchedule &h, const GivenSchedule &g) {
@@ -379,6 +460,8 @@ int build_schedule(const sptrsv_csr *A, const sptrsv_analyze_opts &o, HostSchedu
             h.loc_nb = given->loc_nb;
             h.loc_blk.assign(given->loc_blk, given->loc_blk + n);
             h.loc_lidx.assign(given->loc_lidx, given->loc_lidx + n);
+            h.loc_part = -1;
+            ++h.loc_gen;
         }
         h.schedule_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     } else if (o.mode == SPTRSV_SCHED_LEVELS) {
@@ -685,10 +768,12 @@ int sptrsv_plan_export_parts(const sptrsv_plan *p, int32_t *part) {
     return SPTRSV_OK;
 }
 
-int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
+int sptrsv_block_partition(const sptrsv_csr *A, int32_t kind, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
                            int32_t *position) {
     clear_error();
     if (!A || blocks < 1 || row_cap < 0) return fail(SPTRSV_ERR_ARG, "bad arguments");
+    if (kind != SPTRSV_PART_PARENTS && kind != SPTRSV_PART_RANGES && kind != SPTRSV_PART_GRID)
+        return fail(SPTRSV_ERR_ARG, "kind must be SPTRSV_PART_PARENTS, RANGES or GRID");
     int st = validate_csr(A);
     if (st) return st;
     const int32_t n = A->n;
@@ -702,15 +787,25 @@ int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap,
         rp[i + 1] = int32_t(col.size());
         row_of[i] = i;
     }
+    const int32_t cap = row_cap ? row_cap : std::max<int32_t>(n, 1);
     std::vector<int32_t> blk, lidx, load;
-    if (!local_partition(n, blocks, row_cap ? row_cap : std::max<int32_t>(n, 1), level, nlevels, rp.data(),
-                         col.data(), row_of.data(), blk, lidx, load))
-        return fail(SPTRSV_ERR_ARG, "rows do not fit blocks * row_cap");
+    bool ok = false;
+    if (kind == SPTRSV_PART_RANGES) ok = range_partition(n, blocks, cap, level, nlevels, blk, lidx, load);
+    if (kind == SPTRSV_PART_GRID)
+        ok = grid_partition(n, blocks, cap, level, nlevels, rp.data(), col.data(), row_of.data(), blk, lidx, load);
+    if (kind == SPTRSV_PART_PARENTS || (kind == SPTRSV_PART_GRID && !ok))
+        ok = local_partition(n, blocks, cap, level, nlevels, rp.data(), col.data(), row_of.data(), blk, lidx, load);
+    if (!ok) return fail(SPTRSV_ERR_ARG, "rows do not fit blocks * row_cap");
     if (n) {
         std::memcpy(block_of_row, blk.data(), size_t(n) * sizeof(int32_t));
         std::memcpy(position, lidx.data(), size_t(n) * sizeof(int32_t));
     }
     return SPTRSV_OK;
+}
+
+int sptrsv_local_partition(const sptrsv_csr *A, int32_t blocks, int32_t row_cap, int32_t *block_of_row,
+                           int32_t *position) {
+    return sptrsv_block_partition(A, SPTRSV_PART_PARENTS, blocks, row_cap, block_of_row, position);
 }
 
 void sptrsv_destroy(sptrsv_plan *p) {

@@ -157,7 +157,9 @@ void free_device(sptrsv_plan *p) {
                     d.phase_ent,
                     d.counters, d.flags,    d.work,
                     d.l_rp,     d.l_col,    d.l_perm,    d.l_blk_row, d.l_val,     d.l_dinv, d.l_s32,
-                    d.l_dinv32};
+                    d.l_dinv32,
+                    d.ck_info,  d.ck_blk,   d.ck_col,    d.ck_orow,   d.ck_val,    d.ck_dinv, d.ck_s32,
+                    d.ck_dinv32, d.ck_sblk, d.ck_seg};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     d = DeviceBuffers();
@@ -223,6 +225,11 @@ Kern<T> local_kernel(int lanes, bool pre) {
         case 32: return pre ? k_local<T, 32, tile_for(32), true> : k_local<T, 32, tile_for(32), false>;
         default: return nullptr;
     }
+}
+template <typename T>
+Kern<T> chunks_kernel(int umax, bool waves) {
+    if (waves) return umax <= 4 ? k_waves<T, 4> : k_waves<T, 8>;
+    return umax <= 4 ? k_chunks<T, 4> : k_chunks<T, 8>;
 }
 template <typename T>
 Kern<T> blocks_kernel(int lanes) {
@@ -297,7 +304,9 @@ constexpr size_t kStageSmemMax = 200 * 1024;
 struct LaunchCfg {
     int sync, lanes, threads, grid;
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
-                       // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled)
+                       // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled),
+                       // 6 chunked block-local (polled, one row per lane), 7 the same stepped by wavefront
+    int umax;          // chunked executor: entries per lane kept in registers (4 or 8)
     StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
     bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
@@ -334,6 +343,8 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
     switch (c.kind) {
         case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager, c.short_rows));
         case 5: return RP ? nullptr : reinterpret_cast<const void *>(local_kernel<T>(c.lanes, c.eager));
+        case 6:
+        case 7: return RP ? nullptr : reinterpret_cast<const void *>(chunks_kernel<T>(c.umax, c.kind == 7));
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
         case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
         default:
@@ -366,45 +377,89 @@ int download(const T *dptr, size_t count, std::vector<T> &h) {
     return SPTRSV_OK;
 }
 
-int ensure_local(sptrsv_plan *p, int nb) {
+// The device-order structure back from the device (the caller's CSR is not
+// kept), column ids in the analysed numbering, and device row of every row.
+int download_structure(sptrsv_plan *p, std::vector<int32_t> &rp, std::vector<int32_t> &col,
+                       std::vector<int32_t> &dev_of) {
+    const int32_t n = p->h.n;
+    int st;
+    if ((st = download(p->d.rp, size_t(n) + 1, rp)) || (st = download(p->d.col, size_t(p->nnz_off), col))) return st;
+    if (p->reversed)                                   // back to the analysed factor's numbering
+        for (auto &c : col) c = n - 1 - c;
+    dev_of.assign(n, 0);
+    for (int32_t r = 0; r < n; ++r) dev_of[p->h.dev_perm[r]] = r;
+    return SPTRSV_OK;
+}
+
+// Rows one block may keep in shared memory (FP64 slots if the plan holds FP64 values).
+int local_row_cap(const sptrsv_plan *p, int32_t *cap) {
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    *cap = int32_t((int64_t(optin) - 1024) / ((p->values & SPTRSV_VALUES_F64) ? 8 : 4));
+    return SPTRSV_OK;
+}
+
+// The plan's row -> block partition for nb blocks of kind `part` (SPTRSV_PART_*;
+// AUTO keeps whatever partition the plan holds for nb blocks, else PARENTS).
+int ensure_partition(sptrsv_plan *p, int nb, int part) {
+    HostSchedule &h = p->h;
+    const int32_t n = h.n;
+    // kept (a saved partition too: the launch checks that its blocks fit shared memory)
+    if (h.loc_nb == nb && h.loc_blk.size() == size_t(n) && (part == SPTRSV_PART_AUTO || part == h.loc_part))
+        return SPTRSV_OK;
+    int32_t row_cap = 0;
+    int st;
+    if ((st = local_row_cap(p, &row_cap))) return st;
+    if (part == SPTRSV_PART_AUTO || part == -1) part = SPTRSV_PART_PARENTS;
+    std::vector<int32_t> blk, lidx, load;
+    bool ok;
+    if (part == SPTRSV_PART_RANGES) {
+        ok = range_partition(n, nb, row_cap, h.level, h.nlevels, blk, lidx, load);
+    } else if (part == SPTRSV_PART_PARENTS || part == SPTRSV_PART_GRID) {
+        std::vector<int32_t> rp, col, dev_of;
+        if ((st = download_structure(p, rp, col, dev_of))) return st;
+        ok = part == SPTRSV_PART_GRID &&
+             grid_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk, lidx, load);
+        if (!ok)      // no grid structure: the parents partition (recorded as asked, so it is not rebuilt)
+            ok = local_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk,
+                                 lidx, load);
+    } else {
+        return fail(SPTRSV_ERR_ARG, "partition must be SPTRSV_PART_AUTO, PARENTS, RANGES or GRID");
+    }
+    if (!ok)
+        return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the "
+                                        "shared memory of " + std::to_string(nb) + " blocks");
+    h.loc_nb = nb;
+    h.loc_blk.swap(blk);
+    h.loc_lidx.swap(lidx);
+    h.loc_part = part;
+    ++h.loc_gen;
+    return SPTRSV_OK;
+}
+
+// The layouts are kept while the plan's partition is the one asked for: the
+// checks below are O(1), so a solve pays no host work once they are built.
+bool partition_kept(const sptrsv_plan *p, int nb, int part) {
+    return p->h.loc_nb == nb && (part == SPTRSV_PART_AUTO || part == p->h.loc_part);
+}
+
+int ensure_local(sptrsv_plan *p, int nb, int part) {
     DeviceBuffers &d = p->d;
-    if (d.loc_nb == nb) return SPTRSV_OK;
+    if (d.loc_nb == nb && d.loc_gen == p->h.loc_gen && partition_kept(p, nb, part)) return SPTRSV_OK;
     DeviceGuard g(p->device);
+    int st;
+    if ((st = ensure_partition(p, nb, part))) return st;
+    if (d.loc_nb == nb && d.loc_gen == p->h.loc_gen) return SPTRSV_OK;
     p->device_bytes -= d.loc_bytes;
     free_local(d);
     const HostSchedule &h = p->h;
     const int32_t n = h.n;
     const size_t nnz = size_t(p->nnz_off);
-    int st;
-    // the device-order factor back from the device (the caller's CSR is not kept)
-    std::vector<int32_t> rp, col;
-    if ((st = download(d.rp, size_t(n) + 1, rp)) || (st = download(d.col, nnz, col))) return st;
-    if (p->reversed)                                   // back to the analysed factor's numbering
-        for (auto &c : col) c = n - 1 - c;
-    std::vector<int32_t> dev_of(n);
-    for (int32_t r = 0; r < n; ++r) dev_of[h.dev_perm[r]] = r;
-    // every block keeps all of its rows' values in shared memory: cap the block size
-    int optin = 0;
-    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    const int32_t row_cap = int32_t((int64_t(optin) - 1024) / ((p->values & SPTRSV_VALUES_F64) ? 8 : 4));
-    std::vector<int32_t> blk, lidx, load;
-    bool have = false;
-    if (h.loc_nb == nb && h.loc_blk.size() == size_t(n)) {         // built before, or read from a saved plan
-        blk = h.loc_blk;
-        lidx = h.loc_lidx;
-        load.assign(size_t(nb), 0);
-        for (int32_t v = 0; v < n; ++v) load[size_t(blk[v])]++;
-        have = *std::max_element(load.begin(), load.end()) <= row_cap;
-    }
-    if (!have) {
-        if (!local_partition(n, nb, row_cap, h.level, h.nlevels, rp.data(), col.data(), dev_of.data(), blk, lidx,
-                             load))
-            return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(n) + " rows do not fit the "
-                                            "shared memory of " + std::to_string(nb) + " blocks");
-        p->h.loc_nb = nb;
-        p->h.loc_blk = blk;
-        p->h.loc_lidx = lidx;
-    }
+    std::vector<int32_t> rp, col, dev_of;
+    if ((st = download_structure(p, rp, col, dev_of))) return st;
+    const std::vector<int32_t> &blk = h.loc_blk, &lidx = h.loc_lidx;
+    std::vector<int32_t> load(size_t(nb), 0);
+    for (int32_t v = 0; v < n; ++v) load[size_t(blk[v])]++;
     std::vector<int32_t> bstart(size_t(nb) + 1, 0);
     for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
     // column ids in the block-local order: a parent of the same block -> its
@@ -413,12 +468,15 @@ int ensure_local(sptrsv_plan *p, int nb) {
     int32_t maxrows = 0;
     for (int32_t v = 0; v < n; ++v) lperm[bstart[blk[v]] + lidx[v]] = v;
     for (int32_t b = 0; b < nb; ++b) maxrows = std::max(maxrows, load[b]);
+    int64_t cross = 0;
     for (int32_t t = 0; t < n; ++t) {
         const int32_t v = lperm[t], dr = dev_of[v];
         int32_t o = lrp[t];
         for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q, ++o) {
             const int32_t c = col[q];
-            lcol[o] = blk[c] == blk[v] ? -(lidx[c] + 2) : (p->reversed ? n - 1 - c : c);
+            const bool same = blk[c] == blk[v];
+            cross += !same;
+            lcol[o] = same ? -(lidx[c] + 2) : (p->reversed ? n - 1 - c : c);
             src[o] = q;
         }
         lrp[t + 1] = o;
@@ -437,10 +495,178 @@ int ensure_local(sptrsv_plan *p, int nb) {
         if ((st = local_values_device(p, src, rsrc, &bytes))) return st;
     }
     d.loc_nb = nb;
+    d.loc_gen = h.loc_gen;
     d.loc_smem = size_t(maxrows) * size_t((p->values & SPTRSV_VALUES_F64) ? 8 : 4);
     d.loc_bytes = bytes;
+    d.cross_edges = cross;
+    d.edges = int64_t(nnz);
     p->device_bytes += bytes;
     return SPTRSV_OK;
+}
+
+void free_chunks(DeviceBuffers &d) {
+    void *ptrs[] = {d.ck_info, d.ck_blk, d.ck_col, d.ck_orow, d.ck_val, d.ck_dinv, d.ck_s32, d.ck_dinv32,
+                    d.ck_sblk, d.ck_seg};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    d.ck_info = d.ck_blk = d.ck_col = d.ck_orow = d.ck_sblk = d.ck_seg = nullptr;
+    d.ck_val = d.ck_dinv = nullptr;
+    d.ck_s32 = d.ck_dinv32 = nullptr;
+    d.ck_gen = -1;
+    d.ck_nb = 0;
+    d.ck_width = 0;
+    d.ck_slots = 0;
+    d.ck_bytes = 0;
+}
+
+// out[i] = in[src[i]], 0 where src[i] < 0 (values into the chunked layout)
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather(int64_t count, const int32_t *__restrict__ src,
+                                                const T *__restrict__ in, T *__restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t q = src[i];
+        out[i] = q >= 0 ? in[q] : T(0);
+    }
+}
+
+template <typename T>
+int gather_values(const std::vector<int32_t> &src, const T *in, T **out, int64_t *bytes) {
+    const size_t count = src.size();
+    const size_t nb = count * sizeof(T) + 64;
+    CUDA_TRY(cudaMalloc((void **)out, nb));
+    CUDA_TRY(cudaMemset(*out, 0, nb));
+    *bytes += int64_t(nb);
+    if (!count) return SPTRSV_OK;
+    int32_t *g_src = nullptr;
+    CUDA_TRY(cudaMalloc((void **)&g_src, count * sizeof(int32_t)));
+    cudaError_t e = cudaMemcpy(g_src, src.data(), count * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int grid = int(std::min<size_t>((count + 255) / 256, 8192));
+        k_gather<T><<<grid, 256>>>(int64_t(count), g_src, in, *out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(g_src);
+    if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("chunk values: ") + cudaGetErrorString(e));
+    return SPTRSV_OK;
+}
+
+// Chunked layout of the plan's partition for nb blocks: every block's
+// (wavefront, id) list cut into chunks of up to 32 rows of one wavefront.
+int ensure_chunks(sptrsv_plan *p, int nb, int part) {
+    DeviceBuffers &d = p->d;
+    if (d.ck_nb == nb && d.ck_gen == p->h.loc_gen && partition_kept(p, nb, part)) return SPTRSV_OK;
+    DeviceGuard g(p->device);
+    int st;
+    if ((st = ensure_partition(p, nb, part))) return st;
+    if (d.ck_nb == nb && d.ck_gen == p->h.loc_gen) return SPTRSV_OK;
+    p->device_bytes -= d.ck_bytes;
+    free_chunks(d);
+    const HostSchedule &h = p->h;
+    const int32_t n = h.n;
+    std::vector<int32_t> rp, col, dev_of;
+    if ((st = download_structure(p, rp, col, dev_of))) return st;
+    const std::vector<int32_t> &blk = h.loc_blk, &lidx = h.loc_lidx;
+    std::vector<int32_t> load(size_t(nb), 0);
+    for (int32_t v = 0; v < n; ++v) load[size_t(blk[v])]++;
+    std::vector<int32_t> bstart(size_t(nb) + 1, 0);
+    for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
+    std::vector<int32_t> lperm(n);
+    for (int32_t v = 0; v < n; ++v) lperm[bstart[blk[v]] + lidx[v]] = v;
+    std::vector<int32_t> info, cblk(size_t(nb) + 1, 0), ccol, csrc, corow, crsrc, sblk(size_t(nb) + 1, 0), seg;
+    int64_t ent = 0, cross = 0;
+    int32_t width_max = 0, slots_max = 0;
+    for (int32_t b = 0; b < nb; ++b) {
+        cblk[b] = int32_t(info.size() / 4);
+        sblk[b] = int32_t(seg.size());
+        slots_max = std::max(slots_max, load[b]);
+        for (int32_t t = bstart[b]; t < bstart[b + 1];) {
+            const int32_t l = h.level[lperm[t]];
+            if (t == bstart[b] || h.level[lperm[t - 1]] != l) seg.push_back(int32_t(info.size() / 4));
+            int32_t k = 0, width = 0;
+            while (t + k < bstart[b + 1] && k < 32 && h.level[lperm[t + k]] == l) {
+                const int32_t dr = dev_of[lperm[t + k]];
+                width = std::max(width, rp[dr + 1] - rp[dr]);
+                ++k;
+            }
+            if (ent + int64_t(width) * 32 > int64_t(INT32_MAX) || width > 0xffff)
+                return fail(SPTRSV_ERR_ARG, "chunked executor: too many entries for 32-bit offsets");
+            // every row's entries: parents of other blocks first, then this block's, each in column order
+            std::vector<int32_t> order(size_t(width) * 32, -1);
+            bool remote = false;
+            for (int32_t lane = 0; lane < k; ++lane) {
+                const int32_t dr = dev_of[lperm[t + lane]];
+                int32_t o = 0;
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int32_t q = rp[dr]; q < rp[dr + 1]; ++q)
+                        if ((blk[col[q]] != b) == (pass == 0)) order[size_t(o++) * 32 + lane] = q;
+                remote = remote || (rp[dr + 1] > rp[dr] && blk[col[order[size_t(lane)]]] != b);
+            }
+            info.insert(info.end(), {int32_t(ent), width | (remote ? (1 << 16) : 0), k, t - bstart[b]});
+            for (int32_t u = 0; u < width; ++u)
+                for (int32_t lane = 0; lane < 32; ++lane) {
+                    int32_t c_out = -1, s_out = -1;
+                    const int32_t q = order[size_t(u) * 32 + lane];
+                    if (q >= 0) {
+                        const int32_t c = col[q];
+                        const bool same = blk[c] == b;
+                        cross += !same;
+                        c_out = same ? -(lidx[c] + 2) : (p->reversed ? n - 1 - c : c);
+                        s_out = q;
+                    }
+                    ccol.push_back(c_out);
+                    csrc.push_back(s_out);
+                }
+            for (int32_t lane = 0; lane < 32; ++lane) {
+                const int32_t v = lane < k ? lperm[t + lane] : -1;
+                corow.push_back(v < 0 ? -1 : (p->reversed ? n - 1 - v : v));
+                crsrc.push_back(v < 0 ? -1 : dev_of[v]);
+            }
+            ent += int64_t(width) * 32;
+            width_max = std::max(width_max, width);
+            t += k;
+        }
+    }
+    cblk[nb] = int32_t(info.size() / 4);
+    sblk[nb] = int32_t(seg.size());
+    seg.push_back(cblk[nb]);
+    int64_t bytes = 0;
+    if ((st = upload(sblk, &d.ck_sblk, &bytes)) || (st = upload(seg, &d.ck_seg, &bytes))) return st;
+    if ((st = upload(info, &d.ck_info, &bytes)) || (st = upload(cblk, &d.ck_blk, &bytes)) ||
+        (st = upload(ccol, &d.ck_col, &bytes)) || (st = upload(corow, &d.ck_orow, &bytes)))
+        return st;
+    if (d.val && ((st = gather_values<double>(csrc, d.val, &d.ck_val, &bytes)) ||
+                  (st = gather_values<double>(crsrc, d.dinv, &d.ck_dinv, &bytes))))
+        return st;
+    if (d.s32 && ((st = gather_values<float>(csrc, d.s32, &d.ck_s32, &bytes)) ||
+                  (st = gather_values<float>(crsrc, d.dinv32, &d.ck_dinv32, &bytes))))
+        return st;
+    d.ck_nb = nb;
+    d.ck_gen = h.loc_gen;
+    d.ck_width = width_max;
+    d.ck_slots = size_t(slots_max);
+    d.ck_bytes = bytes;
+    d.cross_edges = cross;
+    d.edges = p->nnz_off;
+    p->device_bytes += bytes;
+    return SPTRSV_OK;
+}
+
+template <typename T>
+void use_chunks(sptrsv_plan *p, SolveArgs<T> &a) {
+    a.col = p->d.ck_col;
+    a.perm = p->d.ck_orow;
+    a.blk_row = p->d.ck_blk;
+    a.chunk = reinterpret_cast<const int4 *>(p->d.ck_info);
+    a.seg_blk = p->d.ck_sblk;
+    a.seg = p->d.ck_seg;
+    if constexpr (std::is_same<T, double>::value) {
+        a.val = p->d.ck_val;
+        a.dinv = p->d.ck_dinv;
+    } else {
+        a.val = p->d.ck_s32;
+        a.dinv = p->d.ck_dinv32;
+    }
 }
 
 template <typename T>
@@ -470,6 +696,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
             if (!o.blocks_per_sm) o.blocks_per_sm = t.blocks_per_sm;
             if (!o.rhs_tile) o.rhs_tile = t.rhs_tile;
             if (!o.eager_sum) o.eager_sum = t.eager_sum;
+            if (!o.partition) o.partition = t.partition;
         }
     }
     c.sync = o.sync;
@@ -497,16 +724,19 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
     if (o.eager_sum < 0 || o.eager_sum > 2) return fail(SPTRSV_ERR_ARG, "eager_sum must be 0, 1 or 2");
     c.eager = o.eager_sum != SPTRSV_EAGER_OFF;
     c.threads = o.threads ? o.threads : 256;
-    const int max_threads = c.sync == SPTRSV_SYNC_LOCAL ? 1024 : 512;
+    const bool chunked = c.sync == SPTRSV_SYNC_CHUNKS || c.sync == SPTRSV_SYNC_WAVES;
+    const bool one_per_sm = c.sync == SPTRSV_SYNC_LOCAL || chunked;
+    if (chunked && !o.threads) c.threads = 512;
+    const int max_threads = one_per_sm ? 1024 : 512;
     if (c.threads < 32 || c.threads > max_threads || c.threads % 32)
-        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL)");
+        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL, CHUNKS)");
     c.win = 0;
     c.smem = 0;
     c.short_rows = p->max_row_off <= 4;
     if (c.sync == SPTRSV_SYNC_LOCAL) {
         if (nrhs != 1 || c.rp) return fail(SPTRSV_ERR_ARG, "the block-local executor solves one right-hand side");
         if (o.blocks_per_sm > 1) return fail(SPTRSV_ERR_ARG, "the block-local executor runs one block per SM");
-        int st = ensure_local(const_cast<sptrsv_plan *>(p), p->num_sms);
+        int st = ensure_local(const_cast<sptrsv_plan *>(p), p->num_sms, o.partition);
         if (st) return st;
         c.kind = 5;
         c.smem = std::max<size_t>(16, p->d.loc_smem);   // sized for FP64 values (FP32 uses part)
@@ -514,6 +744,21 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
         if (c.smem > size_t(optin))
             return fail(SPTRSV_ERR_ARG, "block-local executor: " + std::to_string(p->d.loc_smem) +
+                                            " bytes per block exceed the shared memory of one SM");
+    } else if (chunked) {
+        if (nrhs != 1 || c.rp) return fail(SPTRSV_ERR_ARG, "the chunked executor solves one right-hand side");
+        if (o.blocks_per_sm > 1) return fail(SPTRSV_ERR_ARG, "the chunked executor runs one block per SM");
+        int st = ensure_chunks(const_cast<sptrsv_plan *>(p), p->num_sms, o.partition);
+        if (st) return st;
+        c.kind = c.sync == SPTRSV_SYNC_WAVES ? 7 : 6;
+        c.lanes = 1;
+        c.umax = p->d.ck_width <= 4 ? 4 : 8;
+        if (c.threads > 512) return fail(SPTRSV_ERR_ARG, "the chunked executor runs at most 512 threads per block");
+        c.smem = std::max<size_t>(16, p->d.ck_slots * sizeof(T));
+        int optin = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        if (c.smem > size_t(optin))
+            return fail(SPTRSV_ERR_ARG, "chunked executor: " + std::to_string(c.smem) +
                                             " bytes per block exceed the shared memory of one SM");
     } else if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
     else if (c.sync == SPTRSV_SYNC_GRID) {
@@ -576,7 +821,7 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     cudaError_t e;
     const int nph = int(p->h.phase_row.size()) - 1;
     const void *k = kernel_ptr<T>(c);
-    if (c.kind == 0 || c.kind == 2 || c.kind == 5) {
+    if (c.kind == 0 || c.kind == 2 || c.kind >= 5) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<Kern<T>>(const_cast<void *>(k)), args);
     } else if (c.kind == 4) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<StageKern<T>>(const_cast<void *>(k)), args, c.si, nph, c.win);
@@ -607,6 +852,8 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     a.blk_phase = p->d.blk_phase;
     a.phase_row = p->d.phase_row;
     a.blk_row = nullptr;
+    a.chunk = nullptr;
+    a.seg_blk = a.seg = nullptr;
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;
@@ -668,6 +915,7 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         c.si.bdev = p->d.work;
     }
     if (c.kind == 5) use_local(p, a);
+    if (c.kind == 6 || c.kind == 7) use_chunks(p, a);
     // right-hand-side tiles on the grid executors: internal row-major copies of b
     // and x (original row order), so a tile gathers a parent's values in one load
     const bool rows = c.rp && nrhs > 1 && (c.kind == 0 || c.kind == 1) && p->h.n > 0;
@@ -685,7 +933,7 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         a.x = xr;
         a.ldb = a.ldx = 1;
         a.brs = a.xrs = nrhs;
-    } else if (c.kind == 0 || c.kind == 5) {      // polled solve: x starts as all-ones NaN (not-yet-computed)
+    } else if (c.kind == 0 || c.kind >= 5) {   // polled solve: x starts as all-ones NaN
         CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
     }
     // zero the counters but keep the status word: a device error of an
@@ -773,13 +1021,14 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     a.timeout_ns = (long long)(o.timeout_s * 1e9);
     a.rtol = o.refine_tol;
     if (c.kind == 5) use_local(p, a);
+    if (c.kind == 6 || c.kind == 7) use_chunks(p, a);
     const int M = o.max_iters;
     for (int t = 0; t <= M + 1; ++t) {
         ra.sweep = t;
         k_residual<<<rgrid, 256, 0, s>>>(ra);
         CUDA_TRY(cudaGetLastError());
         if (t > M) break;
-        if (c.kind == 0 || c.kind == 5) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled sweep
+        if (c.kind == 0 || c.kind >= 5) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled
         else CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, sizeof(unsigned long long), s));  // fresh barrier count
         a.refine = t == 0 ? 1 : 2;
         a.sweep = t;
@@ -832,6 +1081,8 @@ int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_repor
     report->lanes = c.lanes;
     report->grid = c.grid;
     report->threads = c.threads;
+    report->cross_edges = c.kind >= 5 ? p->d.cross_edges : -1;
+    report->edges = p->nnz_off;
     if (ctl.status) {
         CUDA_TRY(cudaMemsetAsync(&reinterpret_cast<Ctl *>(p->d.counters)->status, 0, sizeof(int32_t), s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -860,6 +1111,7 @@ void sptrsv_solve_opts_default(sptrsv_solve_opts *o) {
     o->timeout_s = 2.0;
     o->rhs_tile = 0;
     o->eager_sum = SPTRSV_EAGER_AUTO;
+    o->partition = SPTRSV_PART_AUTO;
 }
 
 int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t ld, int32_t dtype,
@@ -917,6 +1169,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
                     c.sync = sync; c.rhs_tile = tile; c.lanes = lanes; c.threads = t;
                     c.blocks_per_sm = one_block ? 0 : bps;
                     c.eager_sum = SPTRSV_EAGER_ON;
+                    if (sync == SPTRSV_SYNC_LOCAL) c.partition = SPTRSV_PART_PARENTS;
                     cands.push_back(c);
                     if ((sync == SPTRSV_SYNC_FLAGS || sync == SPTRSV_SYNC_LOCAL) && tile == 1 && lanes > 1) {
                         c.eager_sum = SPTRSV_EAGER_OFF;
@@ -925,6 +1178,21 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
                 }
         }
     }
+    // chunked executor: both partitions (all candidates of one partition in a row,
+    // so the partition is built once per kind)
+    if (nrhs == 1)
+        for (int part : {SPTRSV_PART_PARENTS, SPTRSV_PART_RANGES, SPTRSV_PART_GRID})
+            for (int sync : {SPTRSV_SYNC_CHUNKS, SPTRSV_SYNC_WAVES})
+            for (int t : {256, 384, 512}) {
+                sptrsv_solve_opts c = o;
+                c.sync = sync;
+                c.rhs_tile = 1;
+                c.lanes = 1;
+                c.threads = t;
+                c.blocks_per_sm = 1;
+                c.partition = part;
+                cands.push_back(c);
+            }
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -963,6 +1231,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     m.blocks_per_sm = best_o.blocks_per_sm;
     m.rhs_tile = best_o.rhs_tile;
     m.eager_sum = best_o.eager_sum;
+    m.partition = best_o.partition;
     m.ms = best_t;
     if (best) *best = best_o;
     if (best_ms) *best_ms = best_t;

@@ -17,6 +17,13 @@
 //             as an all-ones NaN; a published value is the ready signal).
 //  * k_local  persistent grid, rows partitioned over the blocks for locality;
 //             parents of the same block are polled in shared memory.
+//  * k_chunks the block-local partition with one row per lane: a block's rows
+//             are cut into chunks of up to 32 rows of one wavefront, each
+//             chunk is one warp's unit of work and its FP64 arithmetic runs
+//             as full-warp instructions (sliced ELL entries, coalesced).
+//  * k_waves  the same chunks, each block stepping through its own wavefronts
+//             with a block barrier between them; only parents in other blocks
+//             are polled.
 //  * k_stage / k_walk<CTA>  one thread block walks all supersteps, phases
 //             separated by __syncthreads, the phases staged by bulk copies
 //             (small factors; also the batched executor's unit).
@@ -66,6 +73,10 @@ struct SolveArgs {
     const int32_t *__restrict__ blk_phase;
     const int32_t *__restrict__ phase_row;
     const int32_t *__restrict__ blk_row;   // block-local executor: rows of thread block b
+                                           // (chunked executor: its chunks)
+    const int4 *__restrict__ chunk;        // chunked executor: per chunk {entry offset, width, rows, first slot}
+    const int32_t *__restrict__ seg_blk;   // chunked executor: wavefront segments of block b
+    const int32_t *__restrict__ seg;       // first chunk of every segment (one wavefront of one block)
     const T *b;
     T *x;
     int64_t ldb, ldx;
@@ -614,12 +625,14 @@ __device__ __forceinline__ void publish_row(const SolveArgs<T> &a, int orow, T y
     if (a.refine) refine_apply(a, orow, 0, y, dm, xm);
 }
 
-// Bounded-wait bookkeeping shared by the one-row loops: every 64 rounds, give up
-// if another block recorded an error or the wait exceeded the limit.
+// Bounded-wait bookkeeping shared by the polled loops: every 64 rounds, give up
+// if another block recorded an error or the wait exceeded the limit.  The
+// clock starts at the 64th round, not the first: most waits end within a few
+// rounds, and a timer read at their start would sit on the dependency chain.
 __device__ __forceinline__ bool wait_ok(const Ctl *ctl, long long timeout_ns, unsigned &spins, long long &t0,
                                         int lane) {
-    if ((++spins & 63u) != 1) return true;
-    if (spins == 1) {
+    if ((++spins & 63u) != 0) return true;
+    if (spins == 64) {
         t0 = gtimer();
         return true;
     }
@@ -960,6 +973,313 @@ __global__ void __launch_bounds__(1024, 1) k_local(SolveArgs<T> a) {
     if (waits) atomicAdd(&a.ctl->flag_waits, waits);
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
 }
+
+// ----------------------------------------------------------------------------
+// Chunked block-local executor (SPTRSV_SYNC_CHUNKS).  Same partition as the
+// block-local executor (rows of a thread block in (wavefront, id) order, their
+// values kept in shared memory), but a warp works on a CHUNK: up to 32 rows of
+// one wavefront, one row per lane.  The chunk's entries are stored sliced
+// (entry u of lane l at offset + 32 u + l, a coalesced 128/256-byte load per u),
+// so a chunk of width U costs U + 1 warp-wide FP64 instructions for up to 32
+// rows: on this part a warp FP64 instruction holds the SM's FP64 pipe for about
+// 19 cycles however few lanes are active, so packing rows into full warps is
+// what lets a wavefront of a few hundred rows per SM finish in a few hundred
+// cycles.  A chunk waits until the parents of all its rows have landed
+// (integer tests on the polled values only), then runs Eq. 2.1 for every lane
+// at once: x_i = b_i / A_ii - sum_u v'_iu x_c(iu).
+// Chunks of a block are dealt round-robin to its warps in list order; every
+// chunk holds a single wavefront, so the lowest unfinished chunk has finished
+// parents and its warp is either at it or at an earlier chunk of the same
+// wavefront (which cannot wait): with all blocks co-resident the walk cannot
+// deadlock.  Column ids: c >= 0 an original row id polled in global memory,
+// c <= -2 the parent in slot -c - 2 of this block's shared memory, -1 an empty
+// entry (value 0).
+// ----------------------------------------------------------------------------
+// info.y packs the chunk's width (entries per lane, low 16 bits) and whether
+// any of its entries names a parent of another block (bit 16).
+constexpr int kChunkRemote = 1 << 16;
+__device__ __forceinline__ int chunk_width(const int4 &info) { return info.y & 0xffff; }
+
+template <typename T, int UMAX>
+struct ChunkRegs {
+    int4 info;        // entry offset, width | remote flag, rows, first shared-memory slot
+    int orow;         // original row of this lane, -1 for none
+    T b, dinv;        // b_orow and 1 / A_ii (0 for lanes without a row)
+    int c[UMAX];
+    T v[UMAX];
+};
+
+// Two-stage prefetch: the chunk's descriptor and row ids are loaded two chunks
+// ahead, its right-hand side and entries (whose addresses need them) one chunk
+// ahead, so no load at the top of an iteration waits for another load.
+struct ChunkHead {
+    int4 info;
+    int orow;
+};
+
+template <typename T>
+__device__ __forceinline__ void chunk_head(const SolveArgs<T> &a, int ck, int lane, ChunkHead &h) {
+    h.info = __ldg(a.chunk + ck);
+    h.orow = __ldg(a.perm + int64_t(ck) * 32 + lane);
+}
+
+template <typename T, int UMAX>
+__device__ __forceinline__ void chunk_body(const SolveArgs<T> &a, const ChunkHead &h, int ck, int lane,
+                                           ChunkRegs<T, UMAX> &m) {
+    m.info = h.info;
+    m.orow = h.orow;
+    m.dinv = __ldg(a.dinv + int64_t(ck) * 32 + lane);
+    m.b = m.orow >= 0 ? a.b[m.orow] : T(0);
+    const int width = chunk_width(h.info);
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) {
+        if (u < width) {
+            const int64_t q = int64_t(h.info.x) + int64_t(u) * 32 + lane;
+            m.c[u] = __ldg(a.col + q);
+            m.v[u] = __ldg(a.val + q);
+        } else {
+            m.c[u] = -1;
+            m.v[u] = T(0);
+        }
+    }
+}
+
+template <typename T, int UMAX>
+__device__ __forceinline__ void chunk_load(const SolveArgs<T> &a, int ck, int lane, ChunkRegs<T, UMAX> &m) {
+    ChunkHead h;
+    chunk_head(a, ck, lane, h);
+    chunk_body(a, h, ck, lane, m);
+}
+
+// Entries u >= UMAX of a wide chunk, one poll loop per entry (rare: the
+// autotuner keeps factors with long rows on the other executors).
+template <typename T, int UMAX>
+__device__ __noinline__ bool chunk_tail(const SolveArgs<T> &a, const ChunkRegs<T, UMAX> &m, int lane, const T *xs,
+                                        T &acc) {
+    const int width = chunk_width(m.info);
+    for (int u = UMAX; u < width; ++u) {
+        const int64_t q = int64_t(m.info.x) + int64_t(u) * 32 + lane;
+        const int c = __ldg(a.col + q);
+        const T v = __ldg(a.val + q);
+        T xv = T(0);
+        bool pend = false;
+        if (c != -1) {
+            xv = fetch_polled<T, true>(a.x, xs, c);
+            pend = is_sentinel(xv);
+        }
+        unsigned spins = 0;
+        long long t0 = 0;
+        while (__any_sync(0xffffffffu, pend)) {
+            if (pend) {
+                xv = fetch_polled<T, true>(a.x, xs, c);
+                pend = is_sentinel(xv);
+            }
+            if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
+        }
+        acc -= v * xv;
+    }
+    return true;
+}
+
+// A row's entries are stored parents-of-other-blocks first (they usually land
+// first: an upstream block runs ahead of its consumers), then the block's own
+// parents in column order.  Every parent value is requested at once (global
+// loads for other blocks, shared-memory loads for this block); then entry by
+// entry, each is awaited if it was still missing - one load per wait-loop
+// iteration: measured on GB300, re-testing several pending entries per
+// iteration costs 3-4x more cycles per iteration - and folded into the sum
+// right away, so only the last parent's FMA follows its arrival.
+template <typename T, int UMAX>
+__device__ __forceinline__ bool chunk_exec(const SolveArgs<T> &a, const ChunkRegs<T, UMAX> &m, int lane, T *xs,
+                                           unsigned long long &waits, double &dm, double &xm) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const volatile T *vxs = reinterpret_cast<const volatile T *>(xs);
+    const int width = chunk_width(m.info);
+    const bool remote = (m.info.y & kChunkRemote) != 0;     // warp-uniform
+    T xv[UMAX];
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) {
+        if (remote && m.c[u] >= 0) xv[u] = ld_poll(a.x + m.c[u]);
+        else xv[u] = m.c[u] != -1 ? vxs[m.c[u] < -1 ? -m.c[u] - 2 : 0] : T(0);
+    }
+    T acc = m.b * m.dinv;                 // operands loaded a chunk ago: no stall
+    unsigned spins = 0;
+    long long t0 = 0;
+    bool waited = false;
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) {
+        if (u < width) {                  // warp-uniform
+            const int c = m.c[u];
+            bool pend = c != -1 && is_sentinel(xv[u]);
+            if (__any_sync(kAll, pend)) {
+                waited = true;
+                const bool glob = remote && c >= 0;
+                const int slot = c < -1 ? -c - 2 : m.info.w;   // lanes without one read a valid slot
+                do {
+                    T t;
+                    if (glob) t = pend ? ld_poll(a.x + c) : xv[u];
+                    else t = vxs[slot];
+                    if (pend && !is_sentinel(t)) {
+                        xv[u] = t;
+                        pend = false;
+                    }
+                    if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
+                } while (__any_sync(kAll, pend));
+            }
+            acc -= m.v[u] * xv[u];
+        }
+    }
+    if (waited && lane == 0) ++waits;
+    if (width > UMAX && !chunk_tail<T, UMAX>(a, m, lane, xs, acc)) return false;
+    if (m.orow >= 0) {
+        const T y = publishable(acc);
+        reinterpret_cast<volatile T *>(xs)[m.info.w + lane] = y;
+        st_pub(a.x + m.orow, y);
+        if (a.refine) refine_apply(a, m.orow, 0, acc, dm, xm);
+    }
+    return true;
+}
+
+// At most 512 threads: a lane keeps its row, the next chunk's row and its parents'
+// values in registers (more than the 64 a 1024-thread block allows).
+template <typename T, int UMAX>
+__global__ void __launch_bounds__(512, 1) k_chunks(SolveArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c0 = a.blk_row[blockIdx.x], c1 = a.blk_row[blockIdx.x + 1];
+    if (refine_skip(a)) return;
+    int nslots = 0;
+    if (c1 > c0) {
+        const int4 last = __ldg(a.chunk + c1 - 1);
+        nslots = last.w + last.z;
+    }
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) xs[i] = all_ones<T>();
+    __syncthreads();
+    unsigned long long waits = 0;
+    double dm = 0.0, xm = 0.0;
+    ChunkRegs<T, UMAX> cur, nxt;
+    ChunkHead h1, h2;
+    int ck = c0 + w;
+    if (ck < c1) chunk_load(a, ck, lane, cur);
+    if (ck + nw < c1) chunk_head(a, ck + nw, lane, h1);
+    for (; ck < c1; ck += nw) {                      // warp-uniform
+        if (ck + 2 * nw < c1) chunk_head(a, ck + 2 * nw, lane, h2);
+        if (ck + nw < c1) chunk_body(a, h1, ck + nw, lane, nxt);
+        if (!chunk_exec<T, UMAX>(a, cur, lane, xs, waits, dm, xm)) break;
+        cur = nxt;
+        h1 = h2;
+    }
+    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
+// ----------------------------------------------------------------------------
+// Wavefront-stepped form of the chunked executor (SPTRSV_SYNC_WAVES): every
+// block walks its own wavefronts (a segment = the chunks of one wavefront of
+// the block) with one block barrier between them, the Sec. 2.2 BSP superstep
+// at the scale of one SM.  A parent in the same block belongs to an earlier
+// wavefront of the block, so after the barrier it is read from shared memory
+// without any test; only parents of other blocks are polled in global memory,
+// and those loads are issued a wavefront ahead, when the chunk is prefetched
+// (an upstream block usually runs ahead, so they tend to arrive complete).
+// Blocks only ever wait for lower wavefronts, so with every block co-resident
+// the walk cannot deadlock; a failed wait stops the whole block at the next
+// barrier.
+// ----------------------------------------------------------------------------
+template <typename T, int UMAX>
+struct StepRegs {
+    ChunkRegs<T, UMAX> r;
+    T xr[UMAX];       // values of parents in other blocks, loaded with the chunk
+};
+
+template <typename T, int UMAX>
+__device__ __forceinline__ void step_load(const SolveArgs<T> &a, int ck, int lane, StepRegs<T, UMAX> &m) {
+    chunk_load(a, ck, lane, m.r);
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) m.xr[u] = m.r.c[u] >= 0 ? ld_poll(a.x + m.r.c[u]) : T(0);
+}
+
+template <typename T, int UMAX>
+__device__ __forceinline__ bool step_exec(const SolveArgs<T> &a, const StepRegs<T, UMAX> &s, int lane, T *xs,
+                                          unsigned long long &waits, double &dm, double &xm) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const ChunkRegs<T, UMAX> &m = s.r;
+    T xv[UMAX];
+    unsigned pr = 0;
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u) {
+        if (m.c[u] >= 0) {
+            xv[u] = s.xr[u];
+            if (is_sentinel(xv[u])) pr |= 1u << u;
+        } else {
+            xv[u] = m.c[u] != -1 ? xs[-m.c[u] - 2] : T(0);      // written before the last barrier
+        }
+    }
+    if (__any_sync(kAll, pr != 0)) {
+        if (lane == 0) ++waits;
+        unsigned spins = 0;
+        long long t0 = 0;
+        do {
+#pragma unroll
+            for (int u = 0; u < UMAX; ++u)
+                if (pr & (1u << u)) {
+                    const T t = ld_poll(a.x + m.c[u]);
+                    if (!is_sentinel(t)) {
+                        xv[u] = t;
+                        pr &= ~(1u << u);
+                    }
+                }
+            if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
+        } while (__any_sync(kAll, pr != 0));
+    }
+    T acc = m.b * m.dinv;
+#pragma unroll
+    for (int u = 0; u < UMAX; ++u)
+        if (u < chunk_width(m.info)) acc -= m.v[u] * xv[u];
+    if (chunk_width(m.info) > UMAX && !chunk_tail<T, UMAX>(a, m, lane, xs, acc)) return false;
+    if (m.orow >= 0) {
+        const T y = publishable(acc);
+        xs[m.info.w + lane] = y;
+        st_pub(a.x + m.orow, y);
+        if (a.refine) refine_apply(a, m.orow, 0, acc, dm, xm);
+    }
+    return true;
+}
+
+template <typename T, int UMAX>
+__global__ void __launch_bounds__(512, 1) k_waves(SolveArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (refine_skip(a)) return;
+    const int s0 = a.seg_blk[blockIdx.x], s1 = a.seg_blk[blockIdx.x + 1];
+    unsigned long long waits = 0;
+    double dm = 0.0, xm = 0.0;
+    StepRegs<T, UMAX> cur, nxt;
+    bool hc = s0 < s1 && a.seg[s0] + w < a.seg[s0 + 1];
+    if (hc) step_load(a, a.seg[s0] + w, lane, cur);
+    for (int s = s0; s < s1; ++s) {
+        const int ce = a.seg[s + 1];
+        // this warp's first chunk of the next wavefront: rows, columns, values and the
+        // values of its parents in other blocks, loaded while this wavefront runs
+        const bool hn = s + 1 < s1 && ce + w < a.seg[s + 2];
+        if (hn) step_load(a, ce + w, lane, nxt);
+        bool ok = true;
+        if (hc) ok = step_exec<T, UMAX>(a, cur, lane, xs, waits, dm, xm);
+        for (int ck = a.seg[s] + w + nw; ck < ce && ok; ck += nw) {    // wavefronts wider than the block
+            StepRegs<T, UMAX> t;
+            step_load(a, ck, lane, t);
+            ok = step_exec<T, UMAX>(a, t, lane, xs, waits, dm, xm);
+        }
+        if (__syncthreads_or(!ok)) break;
+        cur = nxt;
+        hc = hn;
+    }
+    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
 
 // ----------------------------------------------------------------------------
 // One thread block walks every phase of a factor (phases separated by

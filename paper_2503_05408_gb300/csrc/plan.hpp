@@ -39,6 +39,8 @@ struct HostSchedule {
     // loc_blk[v] = block of row v, loc_lidx[v] = its position in the block's list
     int32_t loc_nb = 0;
     std::vector<int32_t> loc_blk, loc_lidx;
+    int32_t loc_part = 0;            // SPTRSV_PART_* that built it; -1 read from a saved plan
+    int32_t loc_gen = 0;             // bumped whenever the partition changes
     std::vector<int32_t> level, sigma, pi;
     std::vector<int32_t> perm;       // Sec. 5 order: position -> original row
     std::vector<int32_t> dev_perm;   // device order: device row -> original row
@@ -81,6 +83,22 @@ struct DeviceBuffers {
     int32_t *l_rp = nullptr, *l_col = nullptr, *l_perm = nullptr, *l_blk_row = nullptr;
     double *l_val = nullptr, *l_dinv = nullptr;
     float *l_s32 = nullptr, *l_dinv32 = nullptr;
+    int32_t loc_gen = -1;         // partition generation the l_* arrays were built from
+    // chunked executor layout (same partition, cut into chunks of <= 32 rows of
+    // one wavefront): ck_info holds 4 int32 per chunk (entry offset, width | 1 << 16
+    // if an entry names another block's row, rows, first shared-memory slot),
+    // ck_blk the chunk range of every block, entries (each row's other-block
+    // parents first)
+    // sliced (entry u of lane l of a chunk at offset + 32 u + l), one orow/dinv
+    // per chunk lane (-1 / 0 for lanes without a row)
+    int32_t ck_gen = -1, ck_nb = 0, ck_width = 0;
+    size_t ck_slots = 0;          // most rows of one block (shared-memory slots)
+    int64_t ck_bytes = 0;
+    int64_t cross_edges = 0, edges = 0;   // of the current partition
+    int32_t *ck_info = nullptr, *ck_blk = nullptr, *ck_col = nullptr, *ck_orow = nullptr;
+    int32_t *ck_sblk = nullptr, *ck_seg = nullptr;   // wavefront segments: per block, first chunk of each
+    double *ck_val = nullptr, *ck_dinv = nullptr;
+    float *ck_s32 = nullptr, *ck_dinv32 = nullptr;
 };
 
 }  // namespace sptrsv
@@ -103,7 +121,7 @@ struct sptrsv_plan {
     // call being served is selected by sptrsv_solve before it picks a configuration
     struct TunedCfg {
         bool valid = false;
-        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0, rhs_tile = 0, eager_sum = 0;
+        int32_t sync = 0, lanes = 0, threads = 0, blocks_per_sm = 0, rhs_tile = 0, eager_sum = 0, partition = 0;
         double ms = 0.0;
     };
     TunedCfg tuned[16];
@@ -122,6 +140,23 @@ int validate_csr(const sptrsv_csr *A);
 bool local_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
                      const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
                      std::vector<int32_t> &lidx, std::vector<int32_t> &load);
+// Contiguous ranges of row ids: block b takes rows floor(b n / nb) ..
+// floor((b+1) n / nb) - 1, each block's list in (wavefront, id) order.  Same
+// outputs and failure as local_partition.
+bool range_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                     std::vector<int32_t> &blk, std::vector<int32_t> &lidx, std::vector<int32_t> &load);
+// Structured-grid partition: when the off-diagonal offsets of the factor are
+// dominated by nested strides 1 | s1 | s2 (a 3D grid numbered in natural order:
+// x-lines of s1 rows, planes of s2 rows), rows are grouped into pencils along
+// the fastest stride and the (line, plane) index space is cut into TA x TB <= nb
+// rectangular tiles, one per block.  Every dependency then goes to the same
+// tile or one with a larger line or plane index, so the blocks' dependency
+// graph is acyclic and a dependency path crosses at most TA + TB - 2 tiles.
+// Lists in (wavefront, id) order.  Returns false when no such strides exist
+// (or a tile exceeds row_cap); the caller falls back to local_partition.
+bool grid_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<int32_t> &level, int32_t nlevels,
+                    const int32_t *rp, const int32_t *col, const int32_t *row_of, std::vector<int32_t> &blk,
+                    std::vector<int32_t> &lidx, std::vector<int32_t> &load);
 // A schedule read from a saved plan instead of computed (analysed numbering).
 struct GivenSchedule {
     int32_t mode = SPTRSV_SCHED_LEVELS, k = 1, S = 0, sched_blocks = 1, coarse_vertices = 0;

@@ -4,6 +4,7 @@ The library is loaded through its C ABI and asked for a host-only plan
 (device = -1), so the schedules and permutations it exports can be compared
 bit for bit with the oracle's on any machine.
 """
+import networkx as nx
 import numpy as np
 import pytest
 
@@ -204,6 +205,90 @@ def test_local_partition_locality_on_random_window(L):
     r, c = rows[off], A.col[off]
     prev = lv[c] == lv[r] - 1
     assert np.mean(blk[r][prev] == blk[c][prev]) > 0.5
+
+
+def _lists_valid(A, blk, pos, blocks):
+    """Every block's list is a permutation of 0..k-1 in (wavefront, id) order."""
+    lv = np.asarray(oracle.levels(A)[0])
+    assert blk.min() >= 0 and blk.max() < blocks
+    for b in range(blocks):
+        rows = np.nonzero(blk == b)[0]
+        if rows.size == 0:
+            continue
+        order = rows[np.argsort(pos[rows])]
+        assert np.array_equal(np.sort(pos[rows]), np.arange(rows.size))
+        key = lv[order].astype(np.int64) * A.n + order
+        assert np.all(np.diff(key) > 0)
+
+
+def _block_graph_acyclic(A, blk, blocks):
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    off = A.col != rows
+    e = set(zip(blk[A.col[off]].tolist(), blk[rows[off]].tolist()))
+    g = nx.DiGraph([(a, b) for a, b in e if a != b])
+    g.add_nodes_from(range(blocks))
+    return nx.is_directed_acyclic_graph(g), g
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("kind", ["parents", "ranges", "grid"])
+@pytest.mark.parametrize("blocks", [1, 7, 152])
+def test_block_partition_lists(L, name, kind, blocks):
+    A = CASES[name]()
+    blk, pos = sp.block_partition(A, blocks, kind)
+    _lists_valid(A, blk, pos, blocks)
+
+
+def test_parents_kind_is_the_local_partition(L):
+    A = CASES["random_50k"]()
+    for got, want in zip(sp.block_partition(A, 152, "parents"), sp.local_partition(A, 152)):
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("blocks", [3, 152])
+def test_ranges_partition_is_contiguous(L, blocks):
+    A = CASES["random_50k"]()
+    blk, pos = sp.block_partition(A, blocks, "ranges")
+    assert np.array_equal(blk, (np.arange(A.n, dtype=np.int64) * blocks // A.n).astype(np.int32))
+    ok, _ = _block_graph_acyclic(A, blk, blocks)          # dependencies only to later ranges
+    assert ok
+
+
+@pytest.mark.parametrize("m,blocks", [(24, 152), (40, 152), (40, 12), (20, 6)])
+def test_grid_partition_pencil_tiles(L, m, blocks):
+    # the 3D 7-point stencil in natural order has strides 1 | m | m^2: blocks are unions of
+    # whole x-lines forming (y, z) rectangles, the block graph is acyclic and a path crosses
+    # at most TA + TB - 2 blocks
+    A = W.laplace3d_lower(m ** 3, m)
+    blk, pos = sp.block_partition(A, blocks, "grid")
+    _lists_valid(A, blk, pos, blocks)
+    v = np.arange(A.n)
+    line = v // m
+    assert np.all(blk == blk[line * m])                    # whole x-lines
+    y, z = line % m, line // m
+    used = np.unique(blk)
+    assert 2 <= used.size <= blocks
+    spans = []
+    for b in used:
+        ys, zs = y[blk == b], z[blk == b]
+        # a rectangle of (y, z): its row count is the product of its extents (times m)
+        ny, nz = ys.max() - ys.min() + 1, zs.max() - zs.min() + 1
+        assert np.count_nonzero(blk == b) == ny * nz * m
+        spans.append((ys.min(), zs.min()))
+    TA, TB = len({s[0] for s in spans}), len({s[1] for s in spans})
+    assert TA * TB == used.size
+    ok, g = _block_graph_acyclic(A, blk, blocks)
+    assert ok
+    assert nx.dag_longest_path_length(g) <= TA + TB - 2
+
+
+def test_grid_partition_falls_back_without_strides(L):
+    A = CASES["random_50k"]()                              # offsets spread over a 20000-row window
+    for got, want in zip(sp.block_partition(A, 152, "grid"), sp.local_partition(A, 152)):
+        assert np.array_equal(got, want)
+    A2 = W.laplace2d_lower(4096, 64)                       # two strides only: no (line, plane) tiling
+    for got, want in zip(sp.block_partition(A2, 16, "grid"), sp.local_partition(A2, 16)):
+        assert np.array_equal(got, want)
 
 
 # ------------------------------------------------------------ upper and transposed systems
