@@ -97,8 +97,6 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(SPECIAL), default="lap3d_160_f64")
     ap.add_argument("--precision", default=None, help="f64 or f32_refine (batch / single workloads)")
     ap.add_argument("--serve-requests", type=int, default=10_000)
-    ap.add_argument("--baseline-seconds", type=float, default=20.0)
-    ap.add_argument("--serve-baseline-requests", type=int, default=400)
     ap.add_argument("--sync", default=None)
     ap.add_argument("--lanes", type=int, default=None)
     ap.add_argument("--threads", type=int, default=None)
@@ -611,139 +609,168 @@ def run_batch_reference(args):
 
 
 # ------------------------------------------------------------------ serving workload
+SERVE_MODES = (("continuous", "f32_refine"), ("continuous", "f64"), ("serial", "f64"))
+
+
 def _serve_setup(local, nfactors=64):
+    """64 resident factors (n log-uniform in [10k, 2M], mixed kinds) and, per factor, a pool of
+    16 right-hand sides b = A x* formed on the CPU in FP64 (the seeded workload generator) held in
+    pinned host memory, plus a pinned host scratch for the solutions of unchecked requests."""
     import torch
 
     import paper_2503_05408_gb300 as sp
-    dev = f"cuda:{local}"
-    factors, plans, pools, xstars = [], [], [], []
-    g = torch.Generator(device=dev)
+    factors, plans, pools, scratch = [], [], [], []
     for f in range(nfactors):
         A = W.serve_factor(f)
         plans.append(sp.Plan(A, device=local, analyze_on_device=True))
-        g.manual_seed(9000 + f)
-        xs = (torch.rand((16, A.n), generator=g, device=dev, dtype=torch.float64) * 2 - 1).T   # col-major
-        L = torch.sparse_csr_tensor(torch.from_numpy(A.rowptr.astype(np.int64)),
-                                    torch.from_numpy(A.col.astype(np.int64)),
-                                    torch.from_numpy(A.val), size=(A.n, A.n)).to(dev)
-        b = (L @ xs.contiguous()).T.contiguous().T                                           # col-major (n, 16)
+        _, b = W.manufactured_rhs(A, 16, seed=9000 + f)
+        pb = torch.empty((16, A.n), dtype=torch.float64).pin_memory()
+        pb.copy_(torch.from_numpy(np.ascontiguousarray(b.T)))
         factors.append(A)
-        pools.append(b)
-        xstars.append(xs)
-    return factors, plans, pools, xstars
+        pools.append((b, pb))                        # numpy (n, 16) column-major; pinned (16, n) rows
+        scratch.append(torch.empty((16, A.n), dtype=torch.float64).pin_memory())
+    return factors, plans, pools, scratch
 
 
-def _replay(srv, fids, pools, xstars, arrival, fid, nrhs, deadline_s, check_every):
-    """Submit each request at its arrival time; poll completions; check a sample against x*."""
+def _duration_class(levels):
+    return "lt1k_wavefronts" if levels < 1000 else "lt10k_wavefronts" if levels < 10000 else "ge10k_wavefronts"
+
+
+def _replay(srv, fids, pools, scratch, arrival, fid, nrhs, deadline_s, check, on_done):
+    """Submit request i at arrival[i] with host buffers (b from the factor's pinned pool, x into
+    the factor's pinned scratch, or into a buffer of its own when check(i)); poll completions and
+    hand (i, report, x or None) to on_done.  Returns the number submitted."""
     import torch
     t0 = time.perf_counter()
     outstanding = []
-    errs = []
     submitted = 0
-    for i in range(len(arrival)):
-        while time.perf_counter() - t0 < arrival[i]:
-            pass
-        f, r = int(fid[i]), int(nrhs[i])
-        b = pools[f][:, :r]
-        x = torch.empty((r, b.shape[0]), dtype=torch.float64, device=b.device).T
-        rid = srv.submit(fids[f], b, x)
-        outstanding.append((rid, x, f, r, i % check_every == 0))
-        submitted += 1
+
+    def harvest(limit):
+        nonlocal outstanding
         keep = []
         for k, item in enumerate(outstanding):
-            if k >= 64:                              # oldest first; later ones are polled next time
+            if k >= limit:
                 keep.append(item)
                 continue
             rep = srv.poll(item[0])
             if rep is None:
                 keep.append(item)
-            elif item[4]:
-                xv = item[1]
-                xr = xstars[item[2]][:, :item[3]]
-                errs.append(float((xv - xr).abs().max() / xr.abs().max()))
+            else:
+                on_done(item[1], rep, item[2])
         outstanding = keep
+
+    for i in range(len(arrival)):
+        while time.perf_counter() - t0 < arrival[i]:
+            pass
+        f, r = int(fid[i]), int(nrhs[i])
+        pb = pools[f][1]
+        b = pb[0] if r == 1 else pb[:r].T
+        if check(i):
+            own = torch.empty((r, pb.shape[1]), dtype=torch.float64).pin_memory()
+            x = own[0] if r == 1 else own.T
+        else:
+            x = scratch[f][0] if r == 1 else scratch[f][:r].T
+        rid = srv.submit_host(fids[f], b, x)
+        outstanding.append((rid, i, x if check(i) else None))
+        submitted += 1
+        harvest(64)                                  # oldest first; later ones next time
         if time.perf_counter() - t0 > deadline_s:
             break
-    # wait for the rest (bounded)
-    for item in outstanding:
-        remaining = deadline_s + 120 - (time.perf_counter() - t0)
-        if remaining <= 0:
-            break
-        try:
-            srv.wait(item[0], timeout=remaining)
-        except Exception:
-            continue
-        if item[4]:
-            xr = xstars[item[2]][:, :item[3]]
-            errs.append(float((item[1] - xr).abs().max() / xr.abs().max()))
-    return submitted, errs
+    srv.drain(timeout=600)
+    harvest(len(outstanding))
+    return submitted
 
 
 def run_serve(args):
-    """10,000 Poisson requests (2,000/s) against 64 resident factors (n log-uniform in
-    [10k, 2M], mixed kinds), 1-16 RHS each, FP32 sweeps + FP64 refinement, 40 GB budget;
-    compared with the plain FP64 per-request path (one launch per request, one stream)."""
+    """10,000 Poisson requests (2,000/s, seed 1) against 64 resident factors (n log-uniform in
+    [10k, 2M], mixed kinds), 1-16 RHS each, 40 GB HBM budget, b and x in host memory (the
+    copies are part of every request).  The same request stream is served three ways:
+    continuous batching with FP32 sweeps + FP64 refinement, continuous batching in FP64, and
+    the plain FP64 per-request path (one sptrsv_solve per request, one stream, arrival order).
+    Every 200th request gets its own x, checked against the oracle's solution of the same b."""
     # the server's 32 streams need as many hardware queues (the default is 8), or a
     # long launch blocks the launches queued behind it; read at CUDA context creation
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
+    import oracle
     import paper_2503_05408_gb300 as sp
     world, rank, local = dist_info()
     torch.cuda.set_device(local)
     t_setup = time.perf_counter()
-    factors, plans, pools, xstars = _serve_setup(local)
+    factors, plans, pools, scratch = _serve_setup(local)
     setup_s = time.perf_counter() - t_setup
+    levels = [p.stats()["levels"] for p in plans]
     arrival, fid, nrhs = W.serve_requests(args.serve_requests)
     budget = 40 << 30
-    srv = sp.Server(budget, mode="continuous", precision=args.precision or "f32_refine", device=local,
-                    streams=32, max_batch=256)
-    fids = [srv.register(p) for p in plans]
-    # warm-up: one request per factor (module load, first launches)
-    for f in range(len(plans)):
-        b = pools[f][:, :1].contiguous()
-        x = torch.empty_like(b)
-        srv.wait(srv.submit(fids[f], b[:, 0], x[:, 0]), timeout=120)
-    srv.close()
-    srv = sp.Server(budget, mode="continuous", precision=args.precision or "f32_refine", device=local,
-                    streams=32, max_batch=256)
-    fids = [srv.register(p) for p in plans]
-    clocks = ClockSampler(local)
-    clocks.start()
-    t0 = time.perf_counter()
-    submitted, errs = _replay(srv, fids, pools, xstars, arrival, fid, nrhs, deadline_s=120.0, check_every=50)
-    srv.drain(timeout=300)
-    wall = time.perf_counter() - t0
-    clk = clocks.stop()
-    st = srv.stats()
-    srv.close()
-    # plain FP64 per-request baseline on the same stream, bounded in time
-    base = sp.Server(budget, mode="serial", precision="f64", device=local)
-    bf = [base.register(p) for p in plans]
-    nb = min(len(arrival), args.serve_baseline_requests)
-    bsub, berrs = _replay(base, bf, pools, xstars, arrival[:nb], fid[:nb], nrhs[:nb],
-                          deadline_s=args.baseline_seconds, check_every=10)
-    bst = base.stats()
-    base.close()
-    nnz_solved = float(sum(factors[int(f)].nnz * int(r) for f, r in zip(fid[:submitted], nrhs[:submitted])))
-    line = {"metric": "served solves/s (p50/p99 latency)", "value": st["solves_per_s"], "unit": "solves/s",
-            "n_gpus": world, "steps": submitted, "warmup": len(plans), "ms_per_step": 1e3 / max(st["solves_per_s"], 1e-9),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    check_every = 200
+    oracle_x = {}
+
+    def oracle_solution(f, r):
+        if f not in oracle_x:
+            oracle_x[f] = oracle.solve(factors[f], pools[f][0])
+        return oracle_x[f][:, :r]
+
+    modes = {}
+    clk = None
+    wanted = [m for m in SERVE_MODES if args.precision in (None, m[1]) or m[0] == "serial"]
+    for mode, precision in wanted:
+        kw = dict(streams=32, max_batch=256) if mode == "continuous" else {}
+        srv = sp.Server(budget, mode=mode, precision=precision, device=local, **kw)
+        fids = [srv.register(p) for p in plans]
+        for f in range(len(plans)):                  # warm-up: one request per factor
+            pb = pools[f][1]
+            srv.wait(srv.submit_host(fids[f], pb[0], scratch[f][0]), timeout=120)
+        srv.close()
+        srv = sp.Server(budget, mode=mode, precision=precision, device=local, **kw)
+        fids = [srv.register(p) for p in plans]
+        lat = {c: [] for c in ("lt1k_wavefronts", "lt10k_wavefronts", "ge10k_wavefronts")}
+        errs = []
+
+        def on_done(i, rep, x):
+            f, r = int(fid[i]), int(nrhs[i])
+            lat[_duration_class(levels[f])].append(rep["latency_s"])
+            if x is not None:
+                xv = x.numpy().reshape(factors[f].n, -1)
+                errs.append(oracle.rel_error(xv, oracle_solution(f, r)))
+
+        clocks = ClockSampler(local)
+        clocks.start()
+        t0 = time.perf_counter()
+        submitted = _replay(srv, fids, pools, scratch, arrival, fid, nrhs, deadline_s=400.0,
+                            check=lambda i: i % check_every == 0, on_done=on_done)
+        wall = time.perf_counter() - t0
+        c = clocks.stop()
+        clk = clk or c
+        st = srv.stats()
+        srv.close()
+
+        def pct(v, q):
+            return float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
+        modes[f"{mode}_{precision}"] = {
+            "submitted": submitted, "completed": st["completed"], "solves_per_s": st["solves_per_s"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "wall_s": wall,
+            "launches": st["launches"], "mean_batch": st["mean_batch"],
+            "peak_workspace_bytes": st["peak_workspace_bytes"],
+            "per_class": {k: {"requests": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
+                          for k, v in lat.items()},
+            "err_vs_oracle_max": max(errs) if errs else None, "checked": len(errs), "clocks": c}
+    main = modes.get(f"continuous_{args.precision or 'f32_refine'}") or next(iter(modes.values()))
+    plain = modes.get("serial_f64")
+    line = {"metric": "served solves/s (p50/p99 latency)", "value": main["solves_per_s"], "unit": "solves/s",
+            "n_gpus": world, "steps": main["submitted"], "warmup": len(plans),
+            "ms_per_step": 1e3 / max(main["solves_per_s"], 1e-9), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
             "dtype": "f64" if (args.precision or "f32_refine") == "f64" else "f32+f64-refine",
-            "data": "synthetic (seeded generators, Poisson arrivals)",
-            "config": {"workload": "serve_10k", "requests": submitted, "rate_per_s": 2000, "factors": len(plans),
-                       "sum_n": int(sum(A.n for A in factors)), "hbm_budget_gb": 40, "streams": 32,
-                       "setup_s": setup_s},
-            "served": {k: st[k] for k in ("completed", "p50_ms", "p99_ms", "max_ms", "mean_ms", "solves_per_s",
-                                          "launches", "mean_batch", "peak_workspace_bytes")},
-            "served_nnz_per_s": nnz_solved / wall,
-            "served_err_vs_manufactured_max": max(errs) if errs else None,
-            "plain_f64_per_request": {"submitted": bsub, **{k: bst[k] for k in ("completed", "p50_ms", "p99_ms",
-                                                                               "solves_per_s")},
-                                      "err_max": max(berrs) if berrs else None,
-                                      "note": f"first {nb} requests of the same stream (same arrival times); "
-                                              f"completed within {args.baseline_seconds + 120:.0f} s"},
-            "clocks": clk, "gpu_launches": st["launches"]}
+            "data": "synthetic (seeded generators, Poisson arrivals; b formed on the CPU in FP64)",
+            "config": {"workload": "serve_10k", "requests": int(len(arrival)), "rate_per_s": 2000,
+                       "factors": len(plans), "sum_n": int(sum(A.n for A in factors)), "hbm_budget_gb": 40,
+                       "streams": 32, "buffers": "host (pinned), copies inside every request",
+                       "setup_s": setup_s, "checked_every": check_every},
+            "modes": modes,
+            "speedup_vs_plain_f64": (main["solves_per_s"] / plain["solves_per_s"]) if plain else None,
+            "err_vs_oracle": max((m["err_vs_oracle_max"] or 0.0) for m in modes.values()),
+            "clocks": clk, "gpu_launches": main["launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -344,6 +344,8 @@ typedef struct {
                               another thread block (each one global-memory hop; fixed by the
                               partition); the other modes: -1                                  */
     int64_t edges;         /* dependency edges of the factor (off-diagonal entries)            */
+    double latency_s;      /* serving: completion - submission of the request, seconds (for
+                              host-buffer requests the copies included); 0 otherwise            */
 } sptrsv_report;
 
 /* Solve L X = B for nrhs right-hand sides (Eq. 2.1 in the plan's schedule).
@@ -457,6 +459,19 @@ int sptrsv_serve_register(sptrsv_server *server, sptrsv_plan *plan, int32_t *fac
  * Returns at once with req_id; BUDGET if the request could never fit the budget. */
 int sptrsv_serve_submit(sptrsv_server *server, int32_t factor_id, const double *b, double *x,
                         int32_t nrhs, int64_t ld, uint64_t *req_id);
+/* Submit with HOST buffers (the serving boundary of a client that holds b and wants x in
+ * host memory): b_host is n x nrhs column-major with leading dimension ldb, x_host receives
+ * the solution (leading dimension ldx).  When the request is admitted its b is copied into
+ * device staging carved from the HBM budget next to its workspace; after the solve x is
+ * copied back into x_host on the same stream, and the request completes only then: poll and
+ * wait report it done once x_host holds the result, and its latency (serve statistics)
+ * includes both copies.  x_host is passed here, not at poll time, so that the device-to-host
+ * copy is part of the request.  Both buffers must stay valid and x_host unread until the
+ * request completed.  Page-locked buffers (cudaMallocHost, cudaHostRegister) keep the copies
+ * asynchronous; pageable ones work but the dispatcher thread waits for each copy.  Errors as
+ * sptrsv_serve_submit (BUDGET counts the staging too). */
+int sptrsv_serve_submit_host(sptrsv_server *server, int32_t factor_id, const double *b_host, int64_t ldb,
+                             double *x_host, int64_t ldx, int32_t nrhs, uint64_t *req_id);
 /* PENDING until the request finished; then fills `out`, forgets the request and returns its
  * status (0, or e.g. SPTRSV_ERR_NOT_CONVERGED). */
 int sptrsv_serve_poll(sptrsv_server *server, uint64_t req_id, sptrsv_report *out);

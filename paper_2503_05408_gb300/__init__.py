@@ -84,7 +84,8 @@ class Report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("barriers", ctypes.c_int64),
                 ("flag_waits", ctypes.c_int64), ("dnorm", ctypes.c_double), ("sync", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("grid", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("berr", ctypes.c_double), ("cross_edges", ctypes.c_int64), ("edges", ctypes.c_int64)]
+                ("berr", ctypes.c_double), ("cross_edges", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("latency_s", ctypes.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -156,6 +157,8 @@ def lib():
             "sptrsv_serve_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ServeOpts), pp]),
             "sptrsv_serve_register": (ctypes.c_int, [vp, vp, ctypes.POINTER(i32)]),
             "sptrsv_serve_submit": (ctypes.c_int, [vp, i32, vp, vp, i32, i64, ctypes.POINTER(ctypes.c_uint64)]),
+            "sptrsv_serve_submit_host": (ctypes.c_int, [vp, i32, vp, i64, vp, i64, i32,
+                                                        ctypes.POINTER(ctypes.c_uint64)]),
             "sptrsv_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(Report)]),
             "sptrsv_serve_wait": (ctypes.c_int, [vp, ctypes.c_uint64, dbl, ctypes.POINTER(Report)]),
             "sptrsv_serve_drain": (ctypes.c_int, [vp, dbl]),
@@ -479,6 +482,21 @@ class Server:
         rid = ctypes.c_uint64()
         _check(lib().sptrsv_serve_submit(self.handle, int(fid), b.data_ptr(), x.data_ptr(), nrhs, ld,
                                          ctypes.byref(rid)))
+        return rid.value
+
+    def submit_host(self, fid, b, x):
+        """Submit with host buffers: ``b`` and ``x`` are CPU tensors (float64, n or n x nrhs,
+        column-major; pinned memory keeps the copies asynchronous).  ``x`` is written by the
+        server; read it only after poll / wait reported the request done."""
+        if b.is_cuda or x.is_cuda:
+            raise TypeError("submit_host takes CPU tensors")
+        nrhs, ldb = _colmajor_info(b, self.plans[fid].n)
+        nx, ldx = _colmajor_info(x, self.plans[fid].n)
+        if nx != nrhs:
+            raise ValueError("b and x have different numbers of columns")
+        rid = ctypes.c_uint64()
+        _check(lib().sptrsv_serve_submit_host(self.handle, int(fid), b.data_ptr(), ldb, x.data_ptr(), ldx, nrhs,
+                                              ctypes.byref(rid)))
         return rid.value
 
     def poll(self, rid):

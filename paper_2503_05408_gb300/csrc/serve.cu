@@ -1,7 +1,7 @@
 // Continuous-batching serving loop over resident factors.
 //
-// Clients submit solve requests (factor id, device b/x, number of right-hand
-// sides).  A dispatcher thread admits requests in arrival order as soon as
+// Clients submit solve requests (factor id, b/x in device memory or in host
+// memory, number of right-hand sides).  A dispatcher thread admits requests in arrival order as soon as
 // their device workspace fits the remaining HBM budget, packs every admitted
 // request into one launch of the batched executor on a free stream slot, and
 // keeps going while earlier launches still run: requests that arrive while
@@ -42,6 +42,13 @@ struct Request {
     const double *b = nullptr;
     double *x = nullptr;
     int64_t ld = 0;
+    // host requests: b and x live in host memory; they are staged through device
+    // buffers carved from the arena next to the workspace (n x nrhs each, ld = n)
+    bool host = false;
+    const double *b_host = nullptr;
+    double *x_host = nullptr;
+    int64_t ldb_host = 0, ldx_host = 0;
+    size_t io_off = 0;             // offset of the staged b (then x) inside the request's arena block
     double t_arrive = 0.0, t_done = 0.0;
     int32_t state = 0;              // 0 pending, 1 in flight, 2 done
     size_t ws_off = 0, ws_bytes = 0;
@@ -119,6 +126,21 @@ size_t workspace_bytes(const sptrsv_plan *p, int nrhs, bool refine) {
     return (refine ? 2 * v : 0) + bdev;
 }
 
+// Device staging of a host request's b and x (n x nrhs doubles each).
+size_t host_io_bytes(const sptrsv_plan *p, int nrhs) {
+    return 2 * ((size_t(p->h.n) * size_t(nrhs) * sizeof(double) + 255) & ~size_t(255));
+}
+
+// Copies between a host request's buffers and its device staging (column-major).
+cudaError_t stage_in(const Request &r, int32_t n, double *db, cudaStream_t s) {
+    return cudaMemcpy2DAsync(db, size_t(n) * sizeof(double), r.b_host, size_t(r.ldb_host) * sizeof(double),
+                             size_t(n) * sizeof(double), size_t(r.nrhs), cudaMemcpyHostToDevice, s);
+}
+cudaError_t stage_out(const Request &r, int32_t n, const double *dx, cudaStream_t s) {
+    return cudaMemcpy2DAsync(r.x_host, size_t(r.ldx_host) * sizeof(double), dx, size_t(n) * sizeof(double),
+                             size_t(n) * sizeof(double), size_t(r.nrhs), cudaMemcpyDeviceToHost, s);
+}
+
 }  // namespace
 }  // namespace sptrsv
 
@@ -161,7 +183,8 @@ void finish_request(sptrsv_server *S, uint64_t id, const sptrsv_report &rep, dou
     r.state = 2;
     r.t_done = t;
     r.rep = rep;
-    S->arena.release(r.ws_off, r.ws_bytes);
+    r.rep.latency_s = t - r.t_arrive;
+    S->arena.release(r.ws_off, r.ws_bytes);   // workspace and, for host requests, the staging
     S->latencies.push_back(t - r.t_arrive);
     S->t_last = std::max(S->t_last, t);
     ++S->completed;
@@ -223,29 +246,46 @@ bool continuous_step(sptrsv_server *S) {
                 batch_fill_item(it, p, r.nrhs, S->refine, kServeRingBudget);
                 if (batch_item_smem(it, S->refine) > S->smem) it.staged = 0;   // launch smem is fixed
                 size_t off = 0;
-                const size_t need = batch_item_workspace(it, S->refine);
+                const size_t ws = (batch_item_workspace(it, S->refine) + 255) & ~size_t(255);
+                const size_t need = ws + (r.host ? host_io_bytes(p, r.nrhs) : 0);
                 if (!S->arena.alloc(need, off)) break;             // FIFO: wait for memory
                 pit = S->pending.erase(pit);
                 r.state = 1;
                 r.ws_off = off;
                 r.ws_bytes = need;
+                if (r.host) {                                       // staged in the arena after the workspace
+                    r.io_off = off + ws;
+                    r.b = reinterpret_cast<double *>(S->arena.base + r.io_off);
+                    r.x = reinterpret_cast<double *>(S->arena.base + r.io_off + host_io_bytes(p, r.nrhs) / 2);
+                    r.ld = std::max<int64_t>(p->h.n, 1);
+                }
                 it.b = r.b;
                 it.x = r.x;
                 it.ldb = it.ldx = r.ld;
-                if (need) batch_bind_workspace(it, S->arena.base + off, S->refine);
+                if (ws) batch_bind_workspace(it, S->arena.base + off, S->refine);
                 sl.reqs.push_back(id);
                 ++cnt;
             }
         }
         if (cnt == 0) break;
-        cudaError_t e = cudaMemcpyAsync(sl.d_items, sl.h_items, size_t(cnt) * sizeof(BatchItem),
-                                        cudaMemcpyHostToDevice, sl.stream);
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < cnt && e == cudaSuccess; ++i) {          // host requests: b in
+            const Request &r = S->reqs[sl.reqs[i]];
+            if (r.host) e = stage_in(r, S->factors[r.fid]->h.n, const_cast<double *>(r.b), sl.stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sl.d_items, sl.h_items, size_t(cnt) * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                                sl.stream);
         const int grid = std::max(1, std::min(cnt, S->sms * S->per_sm));
         int st = e == cudaSuccess ? batch_launch(sl.d_items, cnt, sl.d_res, sl.d_cursor, S->cfg, grid, S->threads,
                                                  S->smem, sl.stream)
                                   : SPTRSV_ERR_CUDA;
         if (!st) e = cudaMemcpyAsync(sl.h_res, sl.d_res, size_t(cnt) * sizeof(ItemResult), cudaMemcpyDeviceToHost,
                                      sl.stream);
+        for (int i = 0; i < cnt && !st && e == cudaSuccess; ++i) {   // host requests: x out, inside the request
+            const Request &r = S->reqs[sl.reqs[i]];
+            if (r.host) e = stage_out(r, S->factors[r.fid]->h.n, r.x, sl.stream);
+        }
         if (!st && e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
         if (st || e != cudaSuccess) {
             S->worker_error = SPTRSV_ERR_CUDA;
@@ -273,12 +313,32 @@ bool serial_step(sptrsv_server *S) {
         r = S->reqs[id];
     }
     Slot &sl = S->slots[0];
+    sptrsv_plan *p = S->factors[r.fid];
     sptrsv_solve_opts o;
     sptrsv_solve_opts_default(&o);
     o.precision = SPTRSV_PREC_F64;
     sptrsv_report rep{};
-    int st = sptrsv_solve(S->factors[r.fid], r.b, r.x, r.nrhs, r.ld, SPTRSV_F64, &o,
-                          reinterpret_cast<sptrsv_stream>(sl.stream), &rep);
+    int st = SPTRSV_OK;
+    if (r.host) {          // one request at a time: its staging always fits the arena
+        size_t off = 0;
+        const size_t io = host_io_bytes(p, r.nrhs);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (!S->arena.alloc(io, off)) st = SPTRSV_ERR_BUDGET;
+            else S->reqs[id].ws_off = off, S->reqs[id].ws_bytes = io;
+        }
+        r.b = reinterpret_cast<double *>(S->arena.base + off);
+        r.x = reinterpret_cast<double *>(S->arena.base + off + io / 2);
+        r.ld = std::max<int64_t>(p->h.n, 1);
+        if (!st && stage_in(r, p->h.n, const_cast<double *>(r.b), sl.stream) != cudaSuccess) st = SPTRSV_ERR_CUDA;
+    }
+    if (!st)
+        st = sptrsv_solve(p, r.b, r.x, r.nrhs, r.ld, SPTRSV_F64, &o, reinterpret_cast<sptrsv_stream>(sl.stream), &rep);
+    if (!st && r.host) {
+        cudaError_t e = stage_out(r, p->h.n, r.x, sl.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
+        if (e != cudaSuccess) st = SPTRSV_ERR_CUDA;
+    }
     if (st) rep.status = st;
     const double t = now_s();
     std::lock_guard<std::mutex> lk(S->mu);
@@ -402,16 +462,18 @@ int sptrsv_serve_register(sptrsv_server *S, sptrsv_plan *plan, int32_t *factor_i
     return SPTRSV_OK;
 }
 
-int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, double *x, int32_t nrhs,
-                        int64_t ld, uint64_t *req_id) {
-    clear_error();
-    if (!S || !req_id || !b || !x || nrhs < 1) return fail(SPTRSV_ERR_ARG, "bad argument");
+}  // extern "C"
+
+namespace sptrsv {
+namespace {
+int submit_request(sptrsv_server *S, Request r, uint64_t *req_id) {
     if (S->worker_error) return fail(S->worker_error, S->worker_msg);
     std::unique_lock<std::mutex> lk(S->mu);
-    if (factor_id < 0 || factor_id >= int32_t(S->factors.size())) return fail(SPTRSV_ERR_ARG, "unknown factor id");
-    const sptrsv_plan *p = S->factors[factor_id];
-    if (ld < std::max<int64_t>(p->h.n, 1)) return fail(SPTRSV_ERR_ARG, "ld < n");
-    if (!S->arena_mem && S->opts.mode == SPTRSV_SERVE_CONTINUOUS) {
+    if (r.fid < 0 || r.fid >= int32_t(S->factors.size())) return fail(SPTRSV_ERR_ARG, "unknown factor id");
+    const sptrsv_plan *p = S->factors[r.fid];
+    const int64_t n1 = std::max<int64_t>(p->h.n, 1);
+    if (r.host ? (r.ldb_host < n1 || r.ldx_host < n1) : r.ld < n1) return fail(SPTRSV_ERR_ARG, "ld < n");
+    if (!S->arena_mem && (S->opts.mode == SPTRSV_SERVE_CONTINUOUS || r.host)) {
         int prev = -1;
         cudaGetDevice(&prev);
         cudaSetDevice(S->device);
@@ -419,17 +481,12 @@ int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, do
         if (prev >= 0) cudaSetDevice(prev);
         if (st) return st;
     }
-    const size_t need = S->opts.mode == SPTRSV_SERVE_CONTINUOUS ? workspace_bytes(p, nrhs, S->refine) : 0;
+    size_t need = S->opts.mode == SPTRSV_SERVE_CONTINUOUS ? workspace_bytes(p, r.nrhs, S->refine) + 256 : 0;
+    if (r.host) need += host_io_bytes(p, r.nrhs);
     if (need > S->arena.size) {
         ++S->rejected;
         return fail(SPTRSV_ERR_BUDGET, "request workspace exceeds the HBM budget left by the resident factors");
     }
-    Request r;
-    r.fid = factor_id;
-    r.nrhs = nrhs;
-    r.b = b;
-    r.x = x;
-    r.ld = ld;
     r.t_arrive = now_s();
     if (S->t_first < 0) S->t_first = r.t_arrive;
     const uint64_t id = S->next_id++;
@@ -440,6 +497,38 @@ int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, do
     *req_id = id;
     S->cv.notify_all();
     return SPTRSV_OK;
+}
+}  // namespace
+}  // namespace sptrsv
+
+extern "C" {
+
+int sptrsv_serve_submit(sptrsv_server *S, int32_t factor_id, const double *b, double *x, int32_t nrhs,
+                        int64_t ld, uint64_t *req_id) {
+    clear_error();
+    if (!S || !req_id || !b || !x || nrhs < 1) return fail(SPTRSV_ERR_ARG, "bad argument");
+    Request r;
+    r.fid = factor_id;
+    r.nrhs = nrhs;
+    r.b = b;
+    r.x = x;
+    r.ld = ld;
+    return submit_request(S, r, req_id);
+}
+
+int sptrsv_serve_submit_host(sptrsv_server *S, int32_t factor_id, const double *b_host, int64_t ldb, double *x_host,
+                             int64_t ldx, int32_t nrhs, uint64_t *req_id) {
+    clear_error();
+    if (!S || !req_id || !b_host || !x_host || nrhs < 1) return fail(SPTRSV_ERR_ARG, "bad argument");
+    Request r;
+    r.fid = factor_id;
+    r.nrhs = nrhs;
+    r.host = true;
+    r.b_host = b_host;
+    r.x_host = x_host;
+    r.ldb_host = ldb;
+    r.ldx_host = ldx;
+    return submit_request(S, r, req_id);
 }
 
 int sptrsv_serve_poll(sptrsv_server *S, uint64_t req_id, sptrsv_report *out) {

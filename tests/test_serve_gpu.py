@@ -117,3 +117,84 @@ def test_register_after_submit_and_unknown_ids(factors):
     with pytest.raises(sp.SptrsvError):
         srv.poll(123456789)
     srv.close()
+
+
+def _host_pair(b_np, r, pinned, ld_pad=0):
+    """Column-major CPU tensors for b (first r columns) and x (NaN), optional padded ld."""
+    n = b_np.shape[0]
+    ld = n + ld_pad
+    bb = torch.zeros((r, ld), dtype=torch.float64)
+    bb[:, :n] = torch.from_numpy(np.ascontiguousarray(b_np[:, :r].T))
+    xx = torch.full((r, ld), float("nan"), dtype=torch.float64)
+    if pinned:
+        bb, xx = bb.pin_memory(), xx.pin_memory()
+    b, x = bb.T[:n], xx.T[:n]
+    if r == 1 and ld_pad == 0:
+        b, x = bb[0], xx[0]
+    return b, x
+
+
+@pytest.mark.parametrize("mode,precision", [("continuous", "f32_refine"), ("continuous", "f64"), ("serial", "f64")])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_requests_match_the_oracle(factors, mode, precision, pinned):
+    # b and x in host memory: staged through the server's HBM budget, x copied back before
+    # the request completes; mixed with device-buffer requests of the same factors
+    fs, plans, pools = factors
+    srv = sp.Server(8 * GB, mode=mode, precision=precision)
+    fids = [srv.register(p) for p in plans]
+    rng = np.random.default_rng(11)
+    host_jobs, dev_jobs = [], []
+    for k in range(40):
+        f, r = int(rng.integers(0, len(fs))), int(rng.integers(1, 17))
+        if k % 2 == 0:
+            b, x = _host_pair(pools[f][0], r, pinned, ld_pad=3 if k % 4 == 0 else 0)
+            host_jobs.append((srv.submit_host(fids[f], b, x), b, x, f, r))
+        else:
+            dev_jobs.append(_submit(srv, fids, pools, f, r) + (f,))
+    srv.drain()
+    for rid, b, x, f, r in host_jobs:
+        rep = srv.wait(rid)
+        assert rep["status"] == 0
+        xo = oracle.solve(fs[f], pools[f][0][:, :r])
+        assert oracle.rel_error(x.numpy().reshape(fs[f].n, -1) if x.dim() == 1 else x.numpy(), xo) <= F64_TOL
+        assert np.array_equal(b.numpy().reshape(fs[f].n, -1), pools[f][0][:, :r])        # b untouched
+    for rid, x, f in dev_jobs:
+        assert srv.wait(rid)["status"] == 0
+        r = x.shape[1] if x.dim() == 2 else 1
+        assert oracle.rel_error(x.cpu().numpy().reshape(fs[f].n, -1),
+                                oracle.solve(fs[f], pools[f][0][:, :r])) <= F64_TOL
+    st = srv.stats()
+    assert st["completed"] == 40 and st["peak_workspace_bytes"] <= st["arena_bytes"]
+    srv.close()
+
+
+def test_host_buffer_request_same_as_device_request(factors):
+    # the host form runs the same kernel on the same values: identical bits
+    fs, plans, pools = factors
+    srv = sp.Server(8 * GB, precision="f32_refine")
+    fids = [srv.register(p) for p in plans]
+    rid, x_dev = _submit(srv, fids, pools, 4, 7)
+    srv.wait(rid)
+    b, x = _host_pair(pools[4][0], 7, True)
+    srv.wait(srv.submit_host(fids[4], b, x))
+    assert np.array_equal(x.numpy(), x_dev.cpu().numpy())
+    with pytest.raises(TypeError):
+        srv.submit_host(fids[4], pools[4][1][:, :2], pools[4][1][:, :2])     # device tensors: wrong form
+    srv.close()
+
+
+def test_host_buffer_budget_counts_the_staging(factors):
+    fs, plans, pools = factors
+    need = sum(p.stats()["device_bytes"] for p in plans)
+    A = fs[0]
+    # room for the device-buffer request's workspace, not for workspace + staging of b and x
+    ws = 2 * ((A.n * 16 * 4 + 255) // 256 * 256) + (A.n * 16 * 4 + 64 + 255) // 256 * 256 + 256
+    srv = sp.Server(need + ws + 1024, precision="f32_refine")
+    fids = [srv.register(p) for p in plans]
+    rid, x = _submit(srv, fids, pools, 0, 16)
+    assert srv.wait(rid)["status"] == 0
+    b, xh = _host_pair(pools[0][0], 16, False)
+    with pytest.raises(sp.SptrsvError) as e:
+        srv.submit_host(fids[0], b, xh)
+    assert e.value.status == sp.ERR_BUDGET
+    srv.close()
