@@ -786,7 +786,7 @@ def run_serve_reference(args):
 
 
 SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta", "cta_regs": "cta_regs", "local": "local",
-            "chunks": "chunks", "waves": "waves"}
+            "chunks": "chunks"}
 
 
 def main():

@@ -263,21 +263,17 @@ enum {
                                mode (synchronous: device-to-host copy, host pass, upload) and
                                kept in the plan.  ARG if nrhs > 1 or if the rows do not fit the
                                shared memory of the grid's blocks                            */
-    SPTRSV_SYNC_CHUNKS = 6, /* the block-local partition of SYNC_LOCAL executed one row per
+    SPTRSV_SYNC_CHUNKS = 6  /* the block-local partition of SYNC_LOCAL executed one row per
                                lane: each block's (wavefront, id) list is cut into chunks of
                                up to 32 rows of one wavefront, a warp waits until every
                                parent of its chunk has landed and then runs Eq. 2.1 for all
                                of its rows at once (full-warp FP64 instructions; entries
                                stored sliced, 32 lanes per entry slot).  A row's sum runs in a
                                fixed order (parents of other blocks first, then its own block's,
-                               each in column order): the same bits every run.  One right-hand
+                               each in column order): the same bits every run.  Each block first
+                               writes b_i / A_ii of its rows, in chunk order, into the plan's
+                               workspace, so no step waits on a gather of b.  One right-hand
                                side, at most 512 threads per block; ARG as for SYNC_LOCAL    */
-    SPTRSV_SYNC_WAVES = 7   /* the chunks of SYNC_CHUNKS, but every block steps through its
-                               own wavefronts with one block barrier between them (the Sec.
-                               2.2 superstep at the scale of one SM): parents in the same
-                               block are read from shared memory untested, parents in other
-                               blocks are polled, their loads issued a wavefront ahead.
-                               Same results, limits and errors as SYNC_CHUNKS                */
 };
 enum {
     SPTRSV_PART_AUTO = 0,    /* the partition the plan holds (saved, built or tuned), else PARENTS */
@@ -356,6 +352,9 @@ typedef struct {
  *   stream : enqueue on this stream.
  *   report : NULL -> fully asynchronous (device errors surface on the next call
  *            with a report); non-NULL -> the call synchronises `stream` and fills it.
+ * A plan's control words and device workspace (refinement vectors, staged right-hand
+ * sides) are shared by all of its solves: solves of one plan must not run concurrently
+ * (enqueue them on one stream); different plans may run at the same time.
  * Errors: ARG (sizes, dtype/precision without the needed value copy), NO_DEVICE,
  * LAUNCH (grid not co-resident), CUDA, TIMEOUT, NOT_CONVERGED (x still written). */
 int sptrsv_solve(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_t ld,

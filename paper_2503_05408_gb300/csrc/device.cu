@@ -159,7 +159,7 @@ void free_device(sptrsv_plan *p) {
                     d.l_rp,     d.l_col,    d.l_perm,    d.l_blk_row, d.l_val,     d.l_dinv, d.l_s32,
                     d.l_dinv32,
                     d.ck_info,  d.ck_blk,   d.ck_col,    d.ck_orow,   d.ck_val,    d.ck_dinv, d.ck_s32,
-                    d.ck_dinv32, d.ck_sblk, d.ck_seg};
+                    d.ck_dinv32, d.ck_bd};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     d = DeviceBuffers();
@@ -227,8 +227,7 @@ Kern<T> local_kernel(int lanes, bool pre) {
     }
 }
 template <typename T>
-Kern<T> chunks_kernel(int umax, bool waves) {
-    if (waves) return umax <= 4 ? k_waves<T, 4> : k_waves<T, 8>;
+Kern<T> chunks_kernel(int umax) {
     return umax <= 4 ? k_chunks<T, 4> : k_chunks<T, 8>;
 }
 template <typename T>
@@ -305,7 +304,7 @@ struct LaunchCfg {
     int sync, lanes, threads, grid;
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
                        // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled),
-                       // 6 chunked block-local (polled, one row per lane), 7 the same stepped by wavefront
+                       // 6 chunked block-local (polled, one row per lane)
     int umax;          // chunked executor: entries per lane kept in registers (4 or 8)
     StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
@@ -343,8 +342,7 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
     switch (c.kind) {
         case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager, c.short_rows));
         case 5: return RP ? nullptr : reinterpret_cast<const void *>(local_kernel<T>(c.lanes, c.eager));
-        case 6:
-        case 7: return RP ? nullptr : reinterpret_cast<const void *>(chunks_kernel<T>(c.umax, c.kind == 7));
+        case 6: return RP ? nullptr : reinterpret_cast<const void *>(chunks_kernel<T>(c.umax));
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
         case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
         default:
@@ -505,11 +503,11 @@ int ensure_local(sptrsv_plan *p, int nb, int part) {
 }
 
 void free_chunks(DeviceBuffers &d) {
-    void *ptrs[] = {d.ck_info, d.ck_blk, d.ck_col, d.ck_orow, d.ck_val, d.ck_dinv, d.ck_s32, d.ck_dinv32,
-                    d.ck_sblk, d.ck_seg};
+    void *ptrs[] = {d.ck_info, d.ck_blk, d.ck_col, d.ck_orow, d.ck_val, d.ck_dinv, d.ck_s32, d.ck_dinv32, d.ck_bd};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    d.ck_info = d.ck_blk = d.ck_col = d.ck_orow = d.ck_sblk = d.ck_seg = nullptr;
+    d.ck_info = d.ck_blk = d.ck_col = d.ck_orow = nullptr;
+    d.ck_bd = nullptr;
     d.ck_val = d.ck_dinv = nullptr;
     d.ck_s32 = d.ck_dinv32 = nullptr;
     d.ck_gen = -1;
@@ -573,16 +571,14 @@ int ensure_chunks(sptrsv_plan *p, int nb, int part) {
     for (int32_t b = 0; b < nb; ++b) bstart[b + 1] = bstart[b] + load[b];
     std::vector<int32_t> lperm(n);
     for (int32_t v = 0; v < n; ++v) lperm[bstart[blk[v]] + lidx[v]] = v;
-    std::vector<int32_t> info, cblk(size_t(nb) + 1, 0), ccol, csrc, corow, crsrc, sblk(size_t(nb) + 1, 0), seg;
+    std::vector<int32_t> info, cblk(size_t(nb) + 1, 0), ccol, csrc, corow, crsrc;
     int64_t ent = 0, cross = 0;
     int32_t width_max = 0, slots_max = 0;
     for (int32_t b = 0; b < nb; ++b) {
         cblk[b] = int32_t(info.size() / 4);
-        sblk[b] = int32_t(seg.size());
         slots_max = std::max(slots_max, load[b]);
         for (int32_t t = bstart[b]; t < bstart[b + 1];) {
             const int32_t l = h.level[lperm[t]];
-            if (t == bstart[b] || h.level[lperm[t - 1]] != l) seg.push_back(int32_t(info.size() / 4));
             int32_t k = 0, width = 0;
             while (t + k < bstart[b + 1] && k < 32 && h.level[lperm[t + k]] == l) {
                 const int32_t dr = dev_of[lperm[t + k]];
@@ -628,10 +624,7 @@ int ensure_chunks(sptrsv_plan *p, int nb, int part) {
         }
     }
     cblk[nb] = int32_t(info.size() / 4);
-    sblk[nb] = int32_t(seg.size());
-    seg.push_back(cblk[nb]);
     int64_t bytes = 0;
-    if ((st = upload(sblk, &d.ck_sblk, &bytes)) || (st = upload(seg, &d.ck_seg, &bytes))) return st;
     if ((st = upload(info, &d.ck_info, &bytes)) || (st = upload(cblk, &d.ck_blk, &bytes)) ||
         (st = upload(ccol, &d.ck_col, &bytes)) || (st = upload(corow, &d.ck_orow, &bytes)))
         return st;
@@ -641,6 +634,11 @@ int ensure_chunks(sptrsv_plan *p, int nb, int part) {
     if (d.s32 && ((st = gather_values<float>(csrc, d.s32, &d.ck_s32, &bytes)) ||
                   (st = gather_values<float>(crsrc, d.dinv32, &d.ck_dinv32, &bytes))))
         return st;
+    {
+        const size_t bdb = corow.size() * sizeof(double) + 64;
+        CUDA_TRY(cudaMalloc(&d.ck_bd, bdb));
+        bytes += int64_t(bdb);
+    }
     d.ck_nb = nb;
     d.ck_gen = h.loc_gen;
     d.ck_width = width_max;
@@ -658,8 +656,7 @@ void use_chunks(sptrsv_plan *p, SolveArgs<T> &a) {
     a.perm = p->d.ck_orow;
     a.blk_row = p->d.ck_blk;
     a.chunk = reinterpret_cast<const int4 *>(p->d.ck_info);
-    a.seg_blk = p->d.ck_sblk;
-    a.seg = p->d.ck_seg;
+    a.bdc = static_cast<T *>(p->d.ck_bd);
     if constexpr (std::is_same<T, double>::value) {
         a.val = p->d.ck_val;
         a.dinv = p->d.ck_dinv;
@@ -724,7 +721,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
     if (o.eager_sum < 0 || o.eager_sum > 2) return fail(SPTRSV_ERR_ARG, "eager_sum must be 0, 1 or 2");
     c.eager = o.eager_sum != SPTRSV_EAGER_OFF;
     c.threads = o.threads ? o.threads : 256;
-    const bool chunked = c.sync == SPTRSV_SYNC_CHUNKS || c.sync == SPTRSV_SYNC_WAVES;
+    const bool chunked = c.sync == SPTRSV_SYNC_CHUNKS;
     const bool one_per_sm = c.sync == SPTRSV_SYNC_LOCAL || chunked;
     if (chunked && !o.threads) c.threads = 512;
     const int max_threads = one_per_sm ? 1024 : 512;
@@ -750,7 +747,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         if (o.blocks_per_sm > 1) return fail(SPTRSV_ERR_ARG, "the chunked executor runs one block per SM");
         int st = ensure_chunks(const_cast<sptrsv_plan *>(p), p->num_sms, o.partition);
         if (st) return st;
-        c.kind = c.sync == SPTRSV_SYNC_WAVES ? 7 : 6;
+        c.kind = 6;
         c.lanes = 1;
         c.umax = p->d.ck_width <= 4 ? 4 : 8;
         if (c.threads > 512) return fail(SPTRSV_ERR_ARG, "the chunked executor runs at most 512 threads per block");
@@ -853,7 +850,7 @@ SolveArgs<T> base_args(sptrsv_plan *p, const T *val, const T *dinv) {
     a.phase_row = p->d.phase_row;
     a.blk_row = nullptr;
     a.chunk = nullptr;
-    a.seg_blk = a.seg = nullptr;
+    a.bdc = nullptr;
     a.b = nullptr;
     a.x = nullptr;
     a.ldb = a.ldx = 0;
@@ -915,7 +912,7 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         c.si.bdev = p->d.work;
     }
     if (c.kind == 5) use_local(p, a);
-    if (c.kind == 6 || c.kind == 7) use_chunks(p, a);
+    if (c.kind == 6) use_chunks(p, a);
     // right-hand-side tiles on the grid executors: internal row-major copies of b
     // and x (original row order), so a tile gathers a parent's values in one load
     const bool rows = c.rp && nrhs > 1 && (c.kind == 0 || c.kind == 1) && p->h.n > 0;
@@ -1021,7 +1018,7 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     a.timeout_ns = (long long)(o.timeout_s * 1e9);
     a.rtol = o.refine_tol;
     if (c.kind == 5) use_local(p, a);
-    if (c.kind == 6 || c.kind == 7) use_chunks(p, a);
+    if (c.kind == 6) use_chunks(p, a);
     const int M = o.max_iters;
     for (int t = 0; t <= M + 1; ++t) {
         ra.sweep = t;
@@ -1182,10 +1179,9 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     // so the partition is built once per kind)
     if (nrhs == 1)
         for (int part : {SPTRSV_PART_PARENTS, SPTRSV_PART_RANGES, SPTRSV_PART_GRID})
-            for (int sync : {SPTRSV_SYNC_CHUNKS, SPTRSV_SYNC_WAVES})
             for (int t : {256, 384, 512}) {
                 sptrsv_solve_opts c = o;
-                c.sync = sync;
+                c.sync = SPTRSV_SYNC_CHUNKS;
                 c.rhs_tile = 1;
                 c.lanes = 1;
                 c.threads = t;

@@ -21,9 +21,6 @@
 //             are cut into chunks of up to 32 rows of one wavefront, each
 //             chunk is one warp's unit of work and its FP64 arithmetic runs
 //             as full-warp instructions (sliced ELL entries, coalesced).
-//  * k_waves  the same chunks, each block stepping through its own wavefronts
-//             with a block barrier between them; only parents in other blocks
-//             are polled.
 //  * k_stage / k_walk<CTA>  one thread block walks all supersteps, phases
 //             separated by __syncthreads, the phases staged by bulk copies
 //             (small factors; also the batched executor's unit).
@@ -75,8 +72,7 @@ struct SolveArgs {
     const int32_t *__restrict__ blk_row;   // block-local executor: rows of thread block b
                                            // (chunked executor: its chunks)
     const int4 *__restrict__ chunk;        // chunked executor: per chunk {entry offset, width, rows, first slot}
-    const int32_t *__restrict__ seg_blk;   // chunked executor: wavefront segments of block b
-    const int32_t *__restrict__ seg;       // first chunk of every segment (one wavefront of one block)
+    T *bdc;                                // chunked executor: b_i / A_ii in chunk-lane order (plan workspace)
     const T *b;
     T *x;
     int64_t ldb, ldx;
@@ -1004,7 +1000,7 @@ template <typename T, int UMAX>
 struct ChunkRegs {
     int4 info;        // entry offset, width | remote flag, rows, first shared-memory slot
     int orow;         // original row of this lane, -1 for none
-    T b, dinv;        // b_orow and 1 / A_ii (0 for lanes without a row)
+    T bd;             // b_orow / A_ii (0 for lanes without a row)
     int c[UMAX];
     T v[UMAX];
 };
@@ -1028,8 +1024,7 @@ __device__ __forceinline__ void chunk_body(const SolveArgs<T> &a, const ChunkHea
                                            ChunkRegs<T, UMAX> &m) {
     m.info = h.info;
     m.orow = h.orow;
-    m.dinv = __ldg(a.dinv + int64_t(ck) * 32 + lane);
-    m.b = m.orow >= 0 ? a.b[m.orow] : T(0);
+    m.bd = a.bdc[int64_t(ck) * 32 + lane];      // gathered by this block at launch: no dependent load
     const int width = chunk_width(h.info);
 #pragma unroll
     for (int u = 0; u < UMAX; ++u) {
@@ -1102,7 +1097,7 @@ __device__ __forceinline__ bool chunk_exec(const SolveArgs<T> &a, const ChunkReg
         if (remote && m.c[u] >= 0) xv[u] = ld_poll(a.x + m.c[u]);
         else xv[u] = m.c[u] != -1 ? vxs[m.c[u] < -1 ? -m.c[u] - 2 : 0] : T(0);
     }
-    T acc = m.b * m.dinv;                 // operands loaded a chunk ago: no stall
+    T acc = m.bd;
     unsigned spins = 0;
     long long t0 = 0;
     bool waited = false;
@@ -1155,6 +1150,12 @@ __global__ void __launch_bounds__(512, 1) k_chunks(SolveArgs<T> a) {
         nslots = last.w + last.z;
     }
     for (int i = threadIdx.x; i < nslots; i += blockDim.x) xs[i] = all_ones<T>();
+    // b_i / A_ii of this block's rows in chunk-lane order: the gather of b through the
+    // row ids (a dependent load) and the multiply run once here, off every step
+    for (int64_t q = int64_t(c0) * 32 + threadIdx.x; q < int64_t(c1) * 32; q += blockDim.x) {
+        const int orow = __ldg(a.perm + q);
+        a.bdc[q] = orow >= 0 ? a.b[orow] * __ldg(a.dinv + q) : T(0);
+    }
     __syncthreads();
     unsigned long long waits = 0;
     double dm = 0.0, xm = 0.0;
@@ -1173,113 +1174,6 @@ __global__ void __launch_bounds__(512, 1) k_chunks(SolveArgs<T> a) {
     if (waits) atomicAdd(&a.ctl->flag_waits, waits);
     if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
 }
-
-// ----------------------------------------------------------------------------
-// Wavefront-stepped form of the chunked executor (SPTRSV_SYNC_WAVES): every
-// block walks its own wavefronts (a segment = the chunks of one wavefront of
-// the block) with one block barrier between them, the Sec. 2.2 BSP superstep
-// at the scale of one SM.  A parent in the same block belongs to an earlier
-// wavefront of the block, so after the barrier it is read from shared memory
-// without any test; only parents of other blocks are polled in global memory,
-// and those loads are issued a wavefront ahead, when the chunk is prefetched
-// (an upstream block usually runs ahead, so they tend to arrive complete).
-// Blocks only ever wait for lower wavefronts, so with every block co-resident
-// the walk cannot deadlock; a failed wait stops the whole block at the next
-// barrier.
-// ----------------------------------------------------------------------------
-template <typename T, int UMAX>
-struct StepRegs {
-    ChunkRegs<T, UMAX> r;
-    T xr[UMAX];       // values of parents in other blocks, loaded with the chunk
-};
-
-template <typename T, int UMAX>
-__device__ __forceinline__ void step_load(const SolveArgs<T> &a, int ck, int lane, StepRegs<T, UMAX> &m) {
-    chunk_load(a, ck, lane, m.r);
-#pragma unroll
-    for (int u = 0; u < UMAX; ++u) m.xr[u] = m.r.c[u] >= 0 ? ld_poll(a.x + m.r.c[u]) : T(0);
-}
-
-template <typename T, int UMAX>
-__device__ __forceinline__ bool step_exec(const SolveArgs<T> &a, const StepRegs<T, UMAX> &s, int lane, T *xs,
-                                          unsigned long long &waits, double &dm, double &xm) {
-    constexpr unsigned kAll = 0xffffffffu;
-    const ChunkRegs<T, UMAX> &m = s.r;
-    T xv[UMAX];
-    unsigned pr = 0;
-#pragma unroll
-    for (int u = 0; u < UMAX; ++u) {
-        if (m.c[u] >= 0) {
-            xv[u] = s.xr[u];
-            if (is_sentinel(xv[u])) pr |= 1u << u;
-        } else {
-            xv[u] = m.c[u] != -1 ? xs[-m.c[u] - 2] : T(0);      // written before the last barrier
-        }
-    }
-    if (__any_sync(kAll, pr != 0)) {
-        if (lane == 0) ++waits;
-        unsigned spins = 0;
-        long long t0 = 0;
-        do {
-#pragma unroll
-            for (int u = 0; u < UMAX; ++u)
-                if (pr & (1u << u)) {
-                    const T t = ld_poll(a.x + m.c[u]);
-                    if (!is_sentinel(t)) {
-                        xv[u] = t;
-                        pr &= ~(1u << u);
-                    }
-                }
-            if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
-        } while (__any_sync(kAll, pr != 0));
-    }
-    T acc = m.b * m.dinv;
-#pragma unroll
-    for (int u = 0; u < UMAX; ++u)
-        if (u < chunk_width(m.info)) acc -= m.v[u] * xv[u];
-    if (chunk_width(m.info) > UMAX && !chunk_tail<T, UMAX>(a, m, lane, xs, acc)) return false;
-    if (m.orow >= 0) {
-        const T y = publishable(acc);
-        xs[m.info.w + lane] = y;
-        st_pub(a.x + m.orow, y);
-        if (a.refine) refine_apply(a, m.orow, 0, acc, dm, xm);
-    }
-    return true;
-}
-
-template <typename T, int UMAX>
-__global__ void __launch_bounds__(512, 1) k_waves(SolveArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *xs = reinterpret_cast<T *>(smem_raw);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (refine_skip(a)) return;
-    const int s0 = a.seg_blk[blockIdx.x], s1 = a.seg_blk[blockIdx.x + 1];
-    unsigned long long waits = 0;
-    double dm = 0.0, xm = 0.0;
-    StepRegs<T, UMAX> cur, nxt;
-    bool hc = s0 < s1 && a.seg[s0] + w < a.seg[s0 + 1];
-    if (hc) step_load(a, a.seg[s0] + w, lane, cur);
-    for (int s = s0; s < s1; ++s) {
-        const int ce = a.seg[s + 1];
-        // this warp's first chunk of the next wavefront: rows, columns, values and the
-        // values of its parents in other blocks, loaded while this wavefront runs
-        const bool hn = s + 1 < s1 && ce + w < a.seg[s + 2];
-        if (hn) step_load(a, ce + w, lane, nxt);
-        bool ok = true;
-        if (hc) ok = step_exec<T, UMAX>(a, cur, lane, xs, waits, dm, xm);
-        for (int ck = a.seg[s] + w + nw; ck < ce && ok; ck += nw) {    // wavefronts wider than the block
-            StepRegs<T, UMAX> t;
-            step_load(a, ck, lane, t);
-            ok = step_exec<T, UMAX>(a, t, lane, xs, waits, dm, xm);
-        }
-        if (__syncthreads_or(!ok)) break;
-        cur = nxt;
-        hc = hn;
-    }
-    if (waits) atomicAdd(&a.ctl->flag_waits, waits);
-    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
-}
-
 
 // ----------------------------------------------------------------------------
 // One thread block walks every phase of a factor (phases separated by

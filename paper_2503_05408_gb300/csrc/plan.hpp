@@ -96,9 +96,9 @@ struct DeviceBuffers {
     int64_t ck_bytes = 0;
     int64_t cross_edges = 0, edges = 0;   // of the current partition
     int32_t *ck_info = nullptr, *ck_blk = nullptr, *ck_col = nullptr, *ck_orow = nullptr;
-    int32_t *ck_sblk = nullptr, *ck_seg = nullptr;   // wavefront segments: per block, first chunk of each
     double *ck_val = nullptr, *ck_dinv = nullptr;
     float *ck_s32 = nullptr, *ck_dinv32 = nullptr;
+    void *ck_bd = nullptr;        // workspace: b_i / A_ii per chunk lane (8 bytes a lane, FP32 uses half)
 };
 
 }  // namespace sptrsv

@@ -1,10 +1,8 @@
-"""The chunked block-local executors (SPTRSV_SYNC_CHUNKS, SPTRSV_SYNC_WAVES) against the CPU oracle.
+"""The chunked block-local executor (SPTRSV_SYNC_CHUNKS) against the CPU oracle.
 
 One row per lane; a block's (wavefront, id) list cut into chunks of up to 32
 rows of one wavefront; a chunk waits for all of its parents and then applies
-Eq. 2.1 to every row at once, summing in column order; WAVES steps each block
-through its wavefronts with a block barrier instead of polling its own rows.
-Both are checked: FP64 parity at
+Eq. 2.1 to every row at once, in a fixed order per row.  Checked: FP64 parity at
 1e-12 on every small factor with both partitions and several block sizes, FP32
 sweeps and FP32 + FP64 refinement, bit-identical results across runs, the
 reported cross-block edge count against the host partition, and the full-size
@@ -55,7 +53,7 @@ CASES = {
 }
 
 
-SYNCS = ["chunks", "waves"]
+SYNCS = ["chunks"]
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -74,14 +72,14 @@ def test_chunks_f64_parity(name, partition, threads, sync):
 
 @pytest.mark.parametrize("name", ["lap2d_64x64", "lap3d_40", "random_60k", "banded_20k"])
 def test_chunks_reproducible(name):
-    # every row sums in a fixed order once its parents are in: the same bits on every run,
-    # and the same bits from both forms (same arithmetic, different waiting)
+    # every row sums in a fixed order once its parents are in: the same bits on every run
+    # and for every block size
     A = CASES[name]()
     xs, b = W.manufactured_rhs(A, 1, seed=42)
     plan = sp.Plan(A)
     x1, rep = _solve(plan, b, sync="chunks", threads=512)
     x2, _ = _solve(plan, b, sync="chunks", threads=512)
-    x3, _ = _solve(plan, b, sync="waves", threads=256)
+    x3, _ = _solve(plan, b, sync="chunks", threads=256)
     assert np.array_equal(x1, x2) and np.array_equal(x1, x3)
     assert oracle.rel_error(x1, oracle.solve(A, b)[:, 0]) <= F64_TOL
 

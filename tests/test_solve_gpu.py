@@ -59,7 +59,7 @@ SMALL = {
 
 
 @pytest.mark.parametrize("name", sorted(SMALL))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks"])
 @pytest.mark.parametrize("lanes", [1, 4, 32])
 def test_f64_levels_parity(name, sync, lanes):
     A = SMALL[name]()
@@ -93,7 +93,7 @@ def test_polled_eager_sum_parity(name, lanes, eager, threads, sync):
 
 
 @pytest.mark.parametrize("name", ["lap2d_64x64", "er_30k", "nb_20k", "banded_20k"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks"])
 @pytest.mark.parametrize("k", [1, 8, 152])
 def test_f64_growlocal_parity(name, sync, k):
     A = SMALL[name]()
@@ -109,7 +109,7 @@ def test_f64_growlocal_parity(name, sync, k):
 
 
 @pytest.mark.parametrize("name", ["lap2d_64x64", "random_60k", "nb_20k"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local", "chunks"])
 @pytest.mark.parametrize("blocks", [2, 6, 22])
 def test_f64_block_parallel_schedule_parity(name, sync, blocks):
     # block-parallel GrowLocal (Sec. 3.1): schedule bit-exact, solve within FP64 tolerance
@@ -129,7 +129,7 @@ def test_f64_block_parallel_schedule_parity(name, sync, blocks):
 
 
 @pytest.mark.parametrize("name", ["er_30k", "nb_20k", "lap2d_64x64"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "local", "chunks"])
 @pytest.mark.parametrize("max_weight", [40.0, 500.0])
 def test_f64_funnel_schedule_parity(name, sync, max_weight):
     # Funnel + GrowLocal (Sec. 4): schedule bit-exact, solve within FP64 tolerance
@@ -192,7 +192,7 @@ def test_f32_solve():
         xs, b = W.manufactured_rhs(A, 1, seed=14)
         xo = oracle.solve(A, b)
         plan = sp.Plan(A)
-        for sync in ("grid", "flags", "cta", "local", "chunks", "waves"):
+        for sync in ("grid", "flags", "cta", "local", "chunks"):
             x, rep = solve_gpu(plan, b, dtype=torch.float32, sync=sync)
             assert oracle.rel_error(x, xo) <= 1e-4
 
@@ -202,7 +202,7 @@ def test_edge_sizes(n):
     A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
     b = np.ones((n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta", "cta_regs", "local", "chunks", "waves"):
+    for sync in ("grid", "flags", "cta", "cta_regs", "local", "chunks"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert np.allclose(x[:, 0], 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)
 
@@ -243,7 +243,7 @@ def test_full_size_configs_f64(cfg):
     xo = oracle.solve(A, b)
     assert oracle.rel_error(xo, xs) < 1e-13
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "local", "chunks", "waves"):
+    for sync in ("grid", "flags", "local", "chunks"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert oracle.rel_error(x, xo) <= F64_TOL
 
@@ -282,10 +282,10 @@ REFINE_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(REFINE_CASES))
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks"])
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_refine_parity(name, sync, nrhs):
-    if sync in ("local", "chunks", "waves") and nrhs > 1:
+    if sync in ("local", "chunks") and nrhs > 1:
         pytest.skip("the block-local executors solve one right-hand side")
     A = REFINE_CASES[name]()
     xs, b = W.manufactured_rhs(A, nrhs, seed=21)
@@ -357,7 +357,7 @@ def test_full_size_random_refine():
     A, xs, b = W.config_random_1m()
     xo = oracle.solve(A, b)
     plan = sp.Plan(A)
-    for sync in ("flags", "grid", "local", "chunks", "waves"):
+    for sync in ("flags", "grid", "local", "chunks"):
         x, rep = solve_gpu(plan, b, sync=sync, precision="f32_refine")
         assert oracle.rel_error(x, xo) <= F64_TOL
 
@@ -380,7 +380,7 @@ UPPER_CASES = ["lap2d_64x64", "lap3d_24", "random_60k", "banded_20k", "er_30k", 
 
 
 @pytest.mark.parametrize("name", UPPER_CASES)
-@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "cta", "cta_regs", "local", "chunks"])
 @pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
 def test_upper_and_transposed_parity(name, sync, tri):
     Lo = SMALL[name]()
@@ -406,7 +406,7 @@ def test_upper_multi_rhs(tri, nrhs, rhs_tile, sync):
 
 
 @pytest.mark.parametrize("tri", ["upper", "lower_transposed"])
-@pytest.mark.parametrize("sync", ["grid", "flags", "local", "chunks", "waves"])
+@pytest.mark.parametrize("sync", ["grid", "flags", "local", "chunks"])
 def test_upper_refine_and_growlocal(tri, sync):
     Lo = W.make_dominant(W.erdos_renyi_lower(30_000, 3e-4, 2))
     U = W.transpose(Lo)
@@ -426,7 +426,7 @@ def test_upper_full_size_3d():
     xo = oracle.solve_upper(U, b)
     assert oracle.rel_error(xo, xs) < 1e-13
     plan = sp.Plan(U, triangle="upper")
-    for sync in ("flags", "local", "chunks", "waves"):
+    for sync in ("flags", "local", "chunks"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert oracle.rel_error(x, xo) <= F64_TOL
 
