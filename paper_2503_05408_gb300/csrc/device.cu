@@ -985,6 +985,7 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     ra.col = p->d.col;
     ra.hi = p->d.val_hi;
     ra.lo = p->d.val_lo;
+    ra.v64 = p->d.val;                 // FP64 values held: one FMA per entry (else the hi/lo split)
     ra.dhi = p->d.diag_hi;
     ra.dlo = p->d.diag_lo;
     ra.perm = p->d.perm;
@@ -1022,7 +1023,8 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
     const int M = o.max_iters;
     for (int t = 0; t <= M + 1; ++t) {
         ra.sweep = t;
-        k_residual<<<rgrid, 256, 0, s>>>(ra);
+        if (ra.v64) k_residual_scaled<<<rgrid, 256, 0, s>>>(ra);
+        else k_residual<<<rgrid, 256, 0, s>>>(ra);
         CUDA_TRY(cudaGetLastError());
         if (t > M) break;
         if (c.kind == 0 || c.kind >= 5) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled

@@ -1691,6 +1691,7 @@ struct ResidualArgs {
     const int32_t *__restrict__ col;
     const float *__restrict__ hi;
     const float *__restrict__ lo;
+    const double *__restrict__ v64;  // A_ij / A_ii in FP64 when the plan holds FP64 values, else null
     const float *__restrict__ dhi;
     const float *__restrict__ dlo;
     const int32_t *__restrict__ perm;
@@ -1742,6 +1743,55 @@ __device__ __forceinline__ void residual_flush(const ResidualArgs &a, double rm,
         atomicMax(&a.ctl->rmax[a.sweep], (unsigned long long)__double_as_longlong(rm));
         if (a.sweep == 0) atomicMax(&a.ctl->bmax, (unsigned long long)__double_as_longlong(bm));
     }
+}
+
+// Residual from the FP64 scaled values v'_ij = A_ij / A_ii (plans holding FP64
+// values): r_i = b_i - A_ii (x_i + sum_j v'_ij x_j), one FP64 FMA per entry and
+// right-hand side for every row length, plus one per row for A_ii = hi + lo.
+// Same bytes per entry as the hi/lo split (8-byte value + 4-byte column);
+// v'_ij carries one rounding, so r keeps FP64 accuracy.  Thread per row; short
+// rows keep their columns and values in registers for all right-hand sides.
+static __global__ void __launch_bounds__(256) k_residual_scaled(ResidualArgs a) {
+    if (residual_skip(a)) return;
+    double rm = 0.0, bm = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    constexpr int kRes = 8;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.n; r += stride) {
+        const int o = __ldg(a.perm + r);
+        const int beg = __ldg(a.rp + r), end = __ldg(a.rp + r + 1);
+        const double d = double(__ldg(a.dhi + r)) + double(__ldg(a.dlo + r));
+        const bool short_row = end - beg <= kRes;
+        int c8[kRes];
+        double v8[kRes];
+        if (short_row && a.sweep > 0) {
+#pragma unroll
+            for (int u = 0; u < kRes; ++u) {
+                const int q = beg + u;
+                c8[u] = q < end ? __ldg(a.col + q) : 0;
+                v8[u] = q < end ? __ldg(a.v64 + q) : 0.0;
+            }
+        }
+        for (int j = 0; j < a.nrhs; ++j) {
+            const double bj = a.b[(int64_t)o * a.b_rs + (int64_t)j * a.ldb];
+            bm = max_abs_bits(bm, bj);
+            double rj = bj;
+            if (a.sweep > 0) {
+                const double *xj = a.x + (int64_t)j * a.ldx;
+                double sum = xj[(int64_t)o * a.x_rs];
+                if (short_row) {
+#pragma unroll
+                    for (int u = 0; u < kRes; ++u)
+                        if (beg + u < end) sum = fma(v8[u], xj[(int64_t)c8[u] * a.x_rs], sum);
+                } else {
+                    for (int q = beg; q < end; ++q) sum = fma(__ldg(a.v64 + q), xj[(int64_t)__ldg(a.col + q) * a.x_rs], sum);
+                }
+                rj = fma(-d, sum, bj);
+            }
+            a.r32[(int64_t)o * a.r_rs + (int64_t)j * a.r_cs] = float(rj);
+            rm = max_abs_bits(rm, rj);
+        }
+    }
+    residual_flush(a, rm, bm);
 }
 
 // Thread per row.  Short rows with several right-hand sides form the row's

@@ -353,6 +353,21 @@ def test_full_size_3d_f64_r32():
     assert oracle.rel_error(x, xo) <= F64_TOL
 
 
+@pytest.mark.parametrize("name", ["random_60k", "er_30k", "lap3d_24"])
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_refine_residual_from_split_values(name, nrhs):
+    # a plan holding FP32 values only forms the FP64 residual from the hi + lo split;
+    # with FP64 values it uses the scaled FP64 values: both reach the oracle at 1e-12
+    A = SMALL[name]()
+    xs, b = W.manufactured_rhs(A, nrhs, seed=25)
+    xo = oracle.solve(A, b)
+    for values in (sp.VALUES_F32, sp.VALUES_F64 | sp.VALUES_F32):
+        plan = sp.Plan(A, values=values)
+        x, rep = solve_gpu(plan, b, sync="flags", precision="f32_refine")
+        assert rep["status"] == 0 and rep["berr"] <= 1e-13
+        assert oracle.rel_error(x, xo) <= F64_TOL
+
+
 def test_full_size_random_refine():
     A, xs, b = W.config_random_1m()
     xo = oracle.solve(A, b)
