@@ -273,7 +273,9 @@ enum {
                                each in column order): the same bits every run.  Each block first
                                writes b_i / A_ii of its rows, in chunk order, into the plan's
                                workspace, so no step waits on a gather of b.  One right-hand
-                               side, at most 512 threads per block; ARG as for SYNC_LOCAL    */
+                               side; at most 768 threads per block when no row has more than
+                               three off-diagonal entries, else 512 (ARG above); ARG as for
+                               SYNC_LOCAL                                                     */
 };
 enum {
     SPTRSV_PART_AUTO = 0,    /* the partition the plan holds (saved, built or tuned), else PARENTS */

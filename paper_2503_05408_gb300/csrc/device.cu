@@ -228,7 +228,7 @@ Kern<T> local_kernel(int lanes, bool pre) {
 }
 template <typename T>
 Kern<T> chunks_kernel(int umax) {
-    return umax <= 4 ? k_chunks<T, 4> : k_chunks<T, 8>;
+    return umax <= 3 ? k_chunks<T, 3> : umax <= 4 ? k_chunks<T, 4> : k_chunks<T, 8>;
 }
 template <typename T>
 Kern<T> blocks_kernel(int lanes) {
@@ -305,7 +305,7 @@ struct LaunchCfg {
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
                        // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled),
                        // 6 chunked block-local (polled, one row per lane)
-    int umax;          // chunked executor: entries per lane kept in registers (4 or 8)
+    int umax;          // chunked executor: entries per lane kept in registers (3, 4 or 8)
     StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
     bool rp;           // lanes map to right-hand sides (multi-RHS tile) instead of entries
@@ -749,8 +749,11 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         if (st) return st;
         c.kind = 6;
         c.lanes = 1;
-        c.umax = p->d.ck_width <= 4 ? 4 : 8;
-        if (c.threads > 512) return fail(SPTRSV_ERR_ARG, "the chunked executor runs at most 512 threads per block");
+        c.umax = p->d.ck_width <= 3 ? 3 : p->d.ck_width <= 4 ? 4 : 8;
+        const int tmax = c.umax <= 3 ? 768 : 512;
+        if (c.threads > tmax)
+            return fail(SPTRSV_ERR_ARG, "the chunked executor runs at most " + std::to_string(tmax) +
+                                            " threads per block for this factor");
         c.smem = std::max<size_t>(16, p->d.ck_slots * sizeof(T));
         int optin = 0;
         CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
@@ -1181,7 +1184,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     // so the partition is built once per kind)
     if (nrhs == 1)
         for (int part : {SPTRSV_PART_PARENTS, SPTRSV_PART_RANGES, SPTRSV_PART_GRID})
-            for (int t : {256, 384, 512}) {
+            for (int t : {256, 384, 512, 768}) {       // 768: chunks of at most three entries
                 sptrsv_solve_opts c = o;
                 c.sync = SPTRSV_SYNC_CHUNKS;
                 c.rhs_tile = 1;

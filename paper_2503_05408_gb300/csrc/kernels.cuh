@@ -333,6 +333,40 @@ __device__ __forceinline__ float ld_poll(const float *p) {
     asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
     return v;
 }
+// Prefetch loads pinned where they are written: the compiler may otherwise sink
+// a read-only load to its use (re-issuing it instead of holding the register),
+// which puts a DRAM round trip on the dependency chain.  ld_pin_nc for data that
+// no thread writes during the kernel, ld_pin for data this block wrote earlier.
+__device__ __forceinline__ int ld_pin_nc(const int *p) {
+    int v;
+    asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_pin_nc(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_pin_nc(const double *p) {
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int4 ld_pin_nc(const int4 *p) {
+    int4 v;
+    asm volatile("ld.global.nc.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_pin(const float *p) {
+    float v;
+    asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_pin(const double *p) {
+    double v;
+    asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_pub(double *p, double v) {
     asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
@@ -1015,8 +1049,8 @@ struct ChunkHead {
 
 template <typename T>
 __device__ __forceinline__ void chunk_head(const SolveArgs<T> &a, int ck, int lane, ChunkHead &h) {
-    h.info = __ldg(a.chunk + ck);
-    h.orow = __ldg(a.perm + int64_t(ck) * 32 + lane);
+    h.info = ld_pin_nc(a.chunk + ck);
+    h.orow = ld_pin_nc(a.perm + int64_t(ck) * 32 + lane);
 }
 
 template <typename T, int UMAX>
@@ -1024,14 +1058,14 @@ __device__ __forceinline__ void chunk_body(const SolveArgs<T> &a, const ChunkHea
                                            ChunkRegs<T, UMAX> &m) {
     m.info = h.info;
     m.orow = h.orow;
-    m.bd = a.bdc[int64_t(ck) * 32 + lane];      // gathered by this block at launch: no dependent load
+    m.bd = ld_pin(a.bdc + int64_t(ck) * 32 + lane);   // gathered by this block at launch: no dependent load
     const int width = chunk_width(h.info);
 #pragma unroll
     for (int u = 0; u < UMAX; ++u) {
         if (u < width) {
             const int64_t q = int64_t(h.info.x) + int64_t(u) * 32 + lane;
-            m.c[u] = __ldg(a.col + q);
-            m.v[u] = __ldg(a.val + q);
+            m.c[u] = ld_pin_nc(a.col + q);
+            m.v[u] = ld_pin_nc(a.val + q);
         } else {
             m.c[u] = -1;
             m.v[u] = T(0);
@@ -1120,6 +1154,13 @@ __device__ __forceinline__ bool chunk_exec(const SolveArgs<T> &a, const ChunkReg
                     }
                     if (!wait_ok(a.ctl, a.timeout_ns, spins, t0, lane)) return false;
                 } while (__any_sync(kAll, pend));
+                // The later entries' parents mostly sit in the chunk that just published
+                // this one: re-read the still-missing shared-memory ones once, so that
+                // they usually need no wait loop of their own.
+#pragma unroll
+                for (int v = u + 1; v < UMAX; ++v)
+                    if (v < width && m.c[v] < -1 && is_sentinel(xv[v]))
+                        xv[v] = vxs[-m.c[v] - 2];
             }
             acc -= m.v[u] * xv[u];
         }
@@ -1135,10 +1176,17 @@ __device__ __forceinline__ bool chunk_exec(const SolveArgs<T> &a, const ChunkReg
     return true;
 }
 
-// At most 512 threads: a lane keeps its row, the next chunk's row and its parents'
-// values in registers (more than the 64 a 1024-thread block allows).
+// Threads per block: a lane keeps its row, the next chunk's row and its parents'
+// values in registers (more than the 64 a 1024-thread block allows).  Chunks of
+// at most three entries per lane fit 768 threads; more warps per block mean each
+// warp takes its next chunk further ahead of that chunk's parents, so the chunk's
+// first reads (those of other blocks' parents are L2 round trips) are back before
+// its parents land.
+template <int UMAX>
+constexpr int chunk_threads_max() { return UMAX <= 3 ? 768 : 512; }
+
 template <typename T, int UMAX>
-__global__ void __launch_bounds__(512, 1) k_chunks(SolveArgs<T> a) {
+__global__ void __launch_bounds__(chunk_threads_max<UMAX>(), 1) k_chunks(SolveArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -70,6 +70,32 @@ def test_chunks_f64_parity(name, partition, threads, sync):
     assert oracle.rel_error(x, xo[:, 0]) <= F64_TOL
 
 
+@pytest.mark.parametrize("name", ["lap2d_64x64", "lap3d_24", "lap3d_40"])
+@pytest.mark.parametrize("partition", ["parents", "ranges", "grid"])
+def test_chunks_768_threads_for_short_rows(name, partition):
+    # rows of at most three off-diagonal entries: up to 768 threads per block
+    A = CASES[name]()
+    xs, b = W.manufactured_rhs(A, 1, seed=47)
+    plan = sp.Plan(A)
+    x, rep = _solve(plan, b, sync="chunks", partition=partition, threads=768)
+    assert rep["status"] == 0 and rep["threads"] == 768
+    assert oracle.rel_error(x, oracle.solve(A, b)[:, 0]) <= F64_TOL
+    x2, _ = _solve(plan, b, sync="chunks", partition=partition, threads=512)
+    assert np.array_equal(x, x2)                      # the same per-row order at any block size
+
+
+def test_chunks_768_threads_rejected_for_longer_rows():
+    A = CASES["banded_20k"]()                         # four off-diagonal entries per row
+    xs, b = W.manufactured_rhs(A, 1, seed=48)
+    plan = sp.Plan(A)
+    bd = torch.from_numpy(np.ascontiguousarray(b[:, 0])).cuda()
+    with pytest.raises(sp.SptrsvError) as e:
+        plan.solve(bd, torch.empty_like(bd), sync="chunks", threads=768)
+    assert e.value.status == sp.ERR_ARG
+    x, rep = _solve(plan, b, sync="chunks", threads=512)
+    assert rep["status"] == 0 and oracle.rel_error(x, oracle.solve(A, b)[:, 0]) <= F64_TOL
+
+
 @pytest.mark.parametrize("name", ["lap2d_64x64", "lap3d_40", "random_60k", "banded_20k"])
 def test_chunks_reproducible(name):
     # every row sums in a fixed order once its parents are in: the same bits on every run
@@ -136,8 +162,9 @@ def test_chunks_full_size_3d_160(partition, sync):
     A, xs, b = W.config_3d_160()
     xo = oracle.solve(A, b)[:, 0]
     plan = sp.Plan(A, analyze_on_device=True)
-    x, rep = _solve(plan, b, sync=sync, partition=partition, threads=384)
-    assert rep["status"] == 0 and oracle.rel_error(x, xo) <= F64_TOL
+    for threads in (384, 768):
+        x, rep = _solve(plan, b, sync=sync, partition=partition, threads=threads)
+        assert rep["status"] == 0 and oracle.rel_error(x, xo) <= F64_TOL
     xr, rep = _solve(plan, b, sync=sync, partition=partition, precision="f32_refine")
     assert rep["status"] == 0 and oracle.rel_error(xr, xo) <= F64_TOL
 
