@@ -502,8 +502,7 @@ void sptrsv_serve_destroy(sptrsv_server *server);
  * that every GPU loading this library holds until the process exits.
  *   - n > SPTRSV_NOALLOC_MAX_ROWS is rejected with SPTRSV_ERR_ARG.
  *   - The first call on a device (with that device current) resolves the
- *     array's device address once; make that first call before any stream
- *     capture on the device.
+ *     array's device address once.
  *   - Every call shares the array; the flags keep the last call's epoch and
  *     the control words are cleared at the start of each call.  Calls that
  *     overlap on the GPU (e.g. on two streams) race: serialise them.
