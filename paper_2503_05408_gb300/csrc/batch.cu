@@ -123,8 +123,10 @@ __device__ __forceinline__ bool walk_variant(const SolveArgs<T> &a, const BatchI
 #undef SPTRSV_WALK
 }
 
-// FP64 residual of one item, r = b - (hi + lo) x, stored as FP32; returns max |r|
-// (and max |b| through bm) over the block.
+// FP64 residual of one item, stored as FP32; returns max |r| (and max |b| through
+// bm) over the block.  With the plan's FP64 scaled values v'_ij = A_ij / A_ii:
+// r_i = b_i - A_ii (x_i + sum_j v'_ij x_j), one FP64 FMA per entry and right-hand
+// side; from the FP32 split alone: r = b - (hi + lo) x, two.
 __device__ double item_residual(const BatchItem &it, bool zero_x, double &bm, double *s_scratch) {
     const double *b = static_cast<const double *>(it.b);
     const double *x = static_cast<const double *>(it.x);
@@ -133,10 +135,16 @@ __device__ double item_residual(const BatchItem &it, bool zero_x, double &bm, do
         const int o = __ldg(it.perm + r);
         const int beg = __ldg(it.rp + r), end = __ldg(it.rp + r + 1);
         const double dh = __ldg(it.dhi + r), dl = __ldg(it.dlo + r);
+        const double d = dh + dl;
         for (int j = 0; j < it.nrhs; ++j) {
             double s = b[o + (int64_t)j * it.ldb];
-            bmax = fmax(bmax, fabs(s));
-            if (!zero_x) {
+            bmax = max_abs_bits(bmax, s);        // integer compare: keeps the FP64 pipe for the sums
+            if (!zero_x && it.val) {
+                const double *xj = x + (int64_t)j * it.ldx;
+                double sum = xj[o];
+                for (int q = beg; q < end; ++q) sum = fma(__ldg(it.val + q), xj[__ldg(it.col + q)], sum);
+                s = fma(-d, sum, s);
+            } else if (!zero_x) {
                 const double *xj = x + (int64_t)j * it.ldx;
                 for (int q = beg; q < end; ++q) {
                     const double xv = xj[__ldg(it.col + q)];
@@ -148,7 +156,7 @@ __device__ double item_residual(const BatchItem &it, bool zero_x, double &bm, do
                 s = fma(-dl, xo, s);
             }
             it.r32[o + (int64_t)j * it.n] = float(s);
-            rm = fmax(rm, fabs(s));
+            rm = max_abs_bits(rm, s);
         }
     }
     bm = block_max(bmax, s_scratch);

@@ -55,6 +55,25 @@ def test_batch_mixed_factors(precision, sync):
             assert rep["sweeps"] >= 2
 
 
+@pytest.mark.parametrize("values", ["f32", "f64|f32"])
+def test_batch_refinement_residual_forms(values):
+    # plans holding FP32 values only form the FP64 residual from the hi + lo split; plans
+    # that also hold FP64 values use the scaled FP64 values: both reach the oracle at 1e-12
+    v = sp.VALUES_F32 if values == "f32" else sp.VALUES_F64 | sp.VALUES_F32
+    factors = MIXED[:8]
+    nrhs = [1, 3, 8, 8, 2, 40, 8, 5]
+    plans = [sp.Plan(A, values=v) for A in factors]
+    batch = sp.Batch(plans, nrhs, precision="f32_refine")
+    rhs = [W.manufactured_rhs(A, r, seed=300 + i)[1] for i, (A, r) in enumerate(zip(factors, nrhs))]
+    bs = [colmajor(b) for b in rhs]
+    xs = [torch.full_like(b, float("nan")) for b in bs]
+    reps = batch.run(bs, xs)
+    torch.cuda.synchronize()
+    for A, b, x, rep in zip(factors, rhs, xs, reps):
+        assert rep["status"] == 0 and rep["sweeps"] >= 2
+        assert oracle.rel_error(x.cpu().numpy().reshape(A.n, -1), oracle.solve(A, b)) <= F64_TOL
+
+
 def test_batch_graph_replay_new_vectors():
     factors = MIXED[:6]
     nrhs = [8] * 6
