@@ -1184,7 +1184,7 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
     // so the partition is built once per kind)
     if (nrhs == 1)
         for (int part : {SPTRSV_PART_PARENTS, SPTRSV_PART_RANGES, SPTRSV_PART_GRID})
-            for (int t : {256, 384, 512, 768}) {       // 768: chunks of at most three entries
+            for (int t : {256, 384, 512, 640, 768}) {  // 640, 768: chunks of at most three entries
                 sptrsv_solve_opts c = o;
                 c.sync = SPTRSV_SYNC_CHUNKS;
                 c.rhs_tile = 1;
