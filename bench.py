@@ -793,7 +793,7 @@ def run_serve_reference(args):
 
 
 SYNC_TAG = {"grid": "grid", "flags": "flags", "cta": "cta", "cta_regs": "cta_regs", "local": "local",
-            "chunks": "chunks"}
+            "chunks": "chunks", "resident": "resident"}
 
 
 def main():

@@ -263,7 +263,7 @@ enum {
                                mode (synchronous: device-to-host copy, host pass, upload) and
                                kept in the plan.  ARG if nrhs > 1 or if the rows do not fit the
                                shared memory of the grid's blocks                            */
-    SPTRSV_SYNC_CHUNKS = 6  /* the block-local partition of SYNC_LOCAL executed one row per
+    SPTRSV_SYNC_CHUNKS = 6, /* the block-local partition of SYNC_LOCAL executed one row per
                                lane: each block's (wavefront, id) list is cut into chunks of
                                up to 32 rows of one wavefront, a warp waits until every
                                parent of its chunk has landed and then runs Eq. 2.1 for all
@@ -276,6 +276,14 @@ enum {
                                side; at most 768 threads per block when no row has more than
                                three off-diagonal entries, else 512 (ARG above); ARG as for
                                SYNC_LOCAL                                                     */
+    SPTRSV_SYNC_RESIDENT = 7 /* one thread block with the whole factor in shared memory (small
+                               factors): it copies the plan's row pointers, row ids, columns,
+                               scaled values and b_i / A_ii once, keeps x there, and walks the
+                               phases one row per thread with a block barrier between phases,
+                               so no dependency step touches global memory.  One right-hand
+                               side, up to 1024 threads; ARG if nrhs > 1 or if the factor needs
+                               more than one SM's shared memory (8 (2 n + m) + 4 (m + 2 n +
+                               phases + 2) bytes in FP64, m = off-diagonal entries)          */
 };
 enum {
     SPTRSV_PART_AUTO = 0,    /* the partition the plan holds (saved, built or tuned), else PARENTS */

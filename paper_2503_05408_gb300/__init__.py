@@ -29,12 +29,13 @@ COARSEN_NONE, COARSEN_FUNNEL = 0, 1
 _COARSEN = {"none": COARSEN_NONE, "funnel": COARSEN_FUNNEL}
 VALUES_F64, VALUES_F32 = 1, 2
 F64, F32 = 0, 1
-SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL, SYNC_CHUNKS = range(7)
+SYNC_AUTO, SYNC_GRID, SYNC_FLAGS, SYNC_CTA, SYNC_CTA_REGS, SYNC_LOCAL, SYNC_CHUNKS, SYNC_RESIDENT = range(8)
 PART_AUTO, PART_PARENTS, PART_RANGES, PART_GRID = 0, 1, 2, 3
 PREC_F64, PREC_F32_REFINE = 0, 1
 
 SYNC_NAMES = {SYNC_AUTO: "auto", SYNC_GRID: "grid", SYNC_FLAGS: "flags", SYNC_CTA: "cta",
-              SYNC_CTA_REGS: "cta_regs", SYNC_LOCAL: "local", SYNC_CHUNKS: "chunks"}
+              SYNC_CTA_REGS: "cta_regs", SYNC_LOCAL: "local", SYNC_CHUNKS: "chunks",
+              SYNC_RESIDENT: "resident"}
 _SYNC = {v: k for k, v in SYNC_NAMES.items()}
 _MODE = {"levels": SCHED_LEVELS, "growlocal": SCHED_GROWLOCAL}
 _PREC = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}

@@ -226,6 +226,12 @@ Kern<T> local_kernel(int lanes, bool pre) {
         default: return nullptr;
     }
 }
+// Shared memory of the resident one-block executor for a plan (bytes).
+size_t resident_smem_bytes(const sptrsv_plan *p, size_t es) {
+    const size_t n = size_t(p->h.n), m = size_t(p->nnz_off), nph = p->h.phase_row.size();
+    return 2 * round16(n * es) + round16(m * es) + round16(m * 4) + round16((n + 1) * 4) + round16(n * 4) +
+           round16(nph * 4);
+}
 template <typename T>
 Kern<T> chunks_kernel(int umax) {
     return umax <= 3 ? k_chunks<T, 3> : umax <= 4 ? k_chunks<T, 4> : k_chunks<T, 8>;
@@ -304,7 +310,8 @@ struct LaunchCfg {
     int sync, lanes, threads, grid;
     int kind;          // 0 flags, 1 walk (grid barrier), 2 blocks (grid barrier), 3 walk (one CTA),
                        // 4 staged walk (one CTA, TMA-staged phases), 5 block-local (polled),
-                       // 6 chunked block-local (polled, one row per lane)
+                       // 6 chunked block-local (polled, one row per lane),
+                       // 7 resident one CTA (whole factor in shared memory)
     int umax;          // chunked executor: entries per lane kept in registers (3, 4 or 8)
     StageInfo si;
     int win;           // shared-memory ring rows for kind 3 (0 = gather from global x)
@@ -343,6 +350,7 @@ const void *kernel_ptr_rp(const LaunchCfg &c) {
         case 0: return reinterpret_cast<const void *>(flags_kernel<T, RP>(c.lanes, c.eager, c.short_rows));
         case 5: return RP ? nullptr : reinterpret_cast<const void *>(local_kernel<T>(c.lanes, c.eager));
         case 6: return RP ? nullptr : reinterpret_cast<const void *>(chunks_kernel<T>(c.umax));
+        case 7: return RP ? nullptr : reinterpret_cast<const void *>(k_resident<T>);
         case 1: return reinterpret_cast<const void *>(walk_kernel<T, true, false, RP>(c.lanes));
         case 2: return RP ? nullptr : reinterpret_cast<const void *>(blocks_kernel<T>(c.lanes));
         default:
@@ -722,11 +730,12 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
     c.eager = o.eager_sum != SPTRSV_EAGER_OFF;
     c.threads = o.threads ? o.threads : 256;
     const bool chunked = c.sync == SPTRSV_SYNC_CHUNKS;
-    const bool one_per_sm = c.sync == SPTRSV_SYNC_LOCAL || chunked;
+    const bool resident = c.sync == SPTRSV_SYNC_RESIDENT;
+    const bool one_per_sm = c.sync == SPTRSV_SYNC_LOCAL || chunked || resident;
     if (chunked && !o.threads) c.threads = 512;
     const int max_threads = one_per_sm ? 1024 : 512;
     if (c.threads < 32 || c.threads > max_threads || c.threads % 32)
-        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL, CHUNKS)");
+        return fail(SPTRSV_ERR_ARG, "threads must be a multiple of 32 in [32, 512] ([32, 1024] for LOCAL, CHUNKS, RESIDENT)");
     c.win = 0;
     c.smem = 0;
     c.short_rows = p->max_row_off <= 4;
@@ -760,6 +769,18 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         if (c.smem > size_t(optin))
             return fail(SPTRSV_ERR_ARG, "chunked executor: " + std::to_string(c.smem) +
                                             " bytes per block exceed the shared memory of one SM");
+    } else if (resident) {
+        if (nrhs != 1 || c.rp) return fail(SPTRSV_ERR_ARG, "the resident executor solves one right-hand side");
+        c.kind = 7;
+        c.lanes = 1;
+        c.smem = resident_smem_bytes(p, sizeof(T));
+        // walking threads: the widest phase rounded up to a warp, at most the block
+        c.win = std::max(32, std::min(c.threads, (p->h.max_phase_rows + 31) / 32 * 32));
+        int optin = 0;
+        CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+        if (c.smem + 1024 > size_t(optin))       // 1 KB of static shared memory (refinement reduction)
+            return fail(SPTRSV_ERR_ARG, "resident executor: the factor needs " + std::to_string(c.smem) +
+                                            " bytes of shared memory, more than one SM has");
     } else if (c.sync == SPTRSV_SYNC_FLAGS) c.kind = 0;
     else if (c.sync == SPTRSV_SYNC_GRID) {
         c.kind = wide_phases(p) ? 1 : 2;
@@ -790,7 +811,7 @@ int choose(const sptrsv_plan *p, const sptrsv_solve_opts &o_in, int32_t nrhs, La
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c.smem));
         if (e != cudaSuccess) return fail(SPTRSV_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e));
     }
-    if (c.kind == 3 || c.kind == 4) {
+    if (c.kind == 3 || c.kind == 4 || c.kind == 7) {
         c.grid = 1;
         return SPTRSV_OK;
     }
@@ -815,19 +836,19 @@ int launch(sptrsv_plan *p, const LaunchCfg &c, const SolveArgs<T> &args, cudaStr
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = (c.kind == 3 || c.kind == 4) ? 0 : 1;   // co-residency guaranteed or error
+    attr[0].val.cooperative = (c.kind == 3 || c.kind == 4 || c.kind == 7) ? 0 : 1;   // co-residency or error
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
     const int nph = int(p->h.phase_row.size()) - 1;
     const void *k = kernel_ptr<T>(c);
-    if (c.kind == 0 || c.kind == 2 || c.kind >= 5) {
+    if (c.kind == 0 || c.kind == 2 || c.kind == 5 || c.kind == 6) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<Kern<T>>(const_cast<void *>(k)), args);
     } else if (c.kind == 4) {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<StageKern<T>>(const_cast<void *>(k)), args, c.si, nph, c.win);
     } else {
         e = cudaLaunchKernelEx(&cfg, reinterpret_cast<WalkKern<T>>(const_cast<void *>(k)), args, nph,
-                               c.kind == 3 ? c.win : 0);
+                               (c.kind == 3 || c.kind == 7) ? c.win : 0);
     }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -933,7 +954,7 @@ int plain_solve(sptrsv_plan *p, const T *val, const T *dinv, const void *b, void
         a.x = xr;
         a.ldb = a.ldx = 1;
         a.brs = a.xrs = nrhs;
-    } else if (c.kind == 0 || c.kind >= 5) {   // polled solve: x starts as all-ones NaN
+    } else if (c.kind == 0 || c.kind == 5 || c.kind == 6) {   // polled solve: x starts as all-ones NaN
         CUDA_TRY(cudaMemset2DAsync(x, size_t(ld) * sizeof(T), 0xFF, size_t(p->h.n) * sizeof(T), size_t(nrhs), s));
     }
     // zero the counters but keep the status word: a device error of an
@@ -1030,7 +1051,7 @@ int refine_solve(sptrsv_plan *p, const double *b, double *x, int32_t nrhs, int64
         else k_residual<<<rgrid, 256, 0, s>>>(ra);
         CUDA_TRY(cudaGetLastError());
         if (t > M) break;
-        if (c.kind == 0 || c.kind >= 5) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled
+        if (c.kind == 0 || c.kind == 5 || c.kind == 6) CUDA_TRY(cudaMemsetAsync(d32, 0xFF, vec, s));   // polled
         else CUDA_TRY(cudaMemsetAsync(p->d.counters, 0, sizeof(unsigned long long), s));  // fresh barrier count
         a.refine = t == 0 ? 1 : 2;
         a.sweep = t;
@@ -1083,7 +1104,7 @@ int read_report(sptrsv_plan *p, const LaunchCfg &c, cudaStream_t s, sptrsv_repor
     report->lanes = c.lanes;
     report->grid = c.grid;
     report->threads = c.threads;
-    report->cross_edges = c.kind >= 5 ? p->d.cross_edges : -1;
+    report->cross_edges = (c.kind == 5 || c.kind == 6) ? p->d.cross_edges : -1;
     report->edges = p->nnz_off;
     if (ctl.status) {
         CUDA_TRY(cudaMemsetAsync(&reinterpret_cast<Ctl *>(p->d.counters)->status, 0, sizeof(int32_t), s));
@@ -1194,6 +1215,17 @@ int sptrsv_autotune(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_
                 c.partition = part;
                 cands.push_back(c);
             }
+    // resident one-block executor: small factors that fit one SM's shared memory
+    if (nrhs == 1)
+        for (int t : {128, 256, 512, 1024}) {
+            sptrsv_solve_opts c = o;
+            c.sync = SPTRSV_SYNC_RESIDENT;
+            c.rhs_tile = 1;
+            c.lanes = 1;
+            c.threads = t;
+            c.blocks_per_sm = 0;
+            cands.push_back(c);
+        }
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));

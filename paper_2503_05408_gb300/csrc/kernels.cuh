@@ -1417,6 +1417,81 @@ __device__ __forceinline__ bool stage_wait(const SolveArgs<T> &a, uint64_t *bar,
     return true;
 }
 
+// ----------------------------------------------------------------------------
+// One thread block with the whole factor resident in shared memory (small
+// factors, one right-hand side).  One thread bulk-copies (cp.async.bulk,
+// completion counted on an mbarrier) the plan's row pointers, row ids,
+// reciprocal diagonals, columns and scaled values into shared memory; the block
+// then forms b_i / A_ii and keeps x by original row id.  The first `nact`
+// threads (the widest phase, rounded up to a warp) walk the phases one row per
+// thread with a barrier of their own between phases, so a step costs a few
+// shared-memory loads, the row's FMAs and one small barrier - no global memory
+// on the dependency chain.  Regions are 16-byte aligned and rounded up to 16
+// bytes (the plan's arrays carry spare bytes past their end); their sum is
+// resident_smem_bytes on the host.
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_resident(SolveArgs<T> a, int nphases, int nact) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar;
+    if (refine_skip(a)) return;
+    const int n = a.n, tid = threadIdx.x, nt = blockDim.x;
+    if (n <= 0) return;
+    const int m = __ldg(a.rp + n);
+    const uint32_t nb_t = uint32_t(round16(size_t(n) * sizeof(T))), nb_v = uint32_t(round16(size_t(m) * sizeof(T)));
+    const uint32_t nb_c = uint32_t(round16(size_t(m) * 4)), nb_r = uint32_t(round16(size_t(n + 1) * 4));
+    const uint32_t nb_p = uint32_t(round16(size_t(n) * 4));
+    unsigned char *q = smem_raw;
+    T *xs = reinterpret_cast<T *>(q);       q += nb_t;      // x by original row id
+    T *bd = reinterpret_cast<T *>(q);       q += nb_t;      // 1 / A_ii, then b_i / A_ii, by device row
+    T *vs = reinterpret_cast<T *>(q);       q += nb_v;      // A_ij / A_ii
+    int *cs = reinterpret_cast<int *>(q);   q += nb_c;      // original column ids
+    int *rps = reinterpret_cast<int *>(q);  q += nb_r;      // row pointers (n + 1)
+    int *pms = reinterpret_cast<int *>(q);  q += nb_p;      // device row -> original row
+    int *phs = reinterpret_cast<int *>(q);                  // phase bounds (nphases + 1)
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&s_bar, nb_t + (m ? nb_v + nb_c : 0u) + nb_r + nb_p);
+        bulk_g2s(bd, a.dinv, nb_t, &s_bar);
+        if (m) {
+            bulk_g2s(vs, a.val, nb_v, &s_bar);
+            bulk_g2s(cs, a.col, nb_c, &s_bar);
+        }
+        bulk_g2s(rps, a.rp, nb_r, &s_bar);
+        bulk_g2s(pms, a.perm, nb_p, &s_bar);
+    }
+    for (int i = tid; i <= nphases; i += nt) phs[i] = __ldg(a.phase_row + i);
+    __syncthreads();                                   // the barrier's initialisation is visible
+    const bool ok = stage_wait(a, &s_bar, 0);          // bounded; records a timeout in the status
+    if (__syncthreads_or(!ok)) return;
+    for (int i = tid; i < n; i += nt) bd[i] = a.b[int64_t(pms[i]) * a.brs] * bd[i];
+    __syncthreads();
+    if (tid < nact) {
+        for (int ph = 0; ph < nphases; ++ph) {
+            const int r1 = phs[ph + 1];
+            for (int r = phs[ph] + tid; r < r1; r += nact) {
+                T acc = bd[r];
+                const int q1 = rps[r + 1];
+                for (int e = rps[r]; e < q1; ++e) acc -= vs[e] * xs[cs[e]];
+                xs[pms[r]] = acc;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(nact) : "memory");   // the walking warps only
+        }
+    }
+    __syncthreads();
+    double dm = 0.0, xm = 0.0;
+    for (int o = tid; o < n; o += nt) {
+        const T y = xs[o];
+        a.x[int64_t(o) * a.xrs] = y;
+        if (a.refine) refine_apply(a, o, 0, y, dm, xm);
+    }
+    if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_bar)) : "memory");
+    if (a.refine) refine_flush(a.ctl, a.sweep, dm, xm);
+}
+
 // Rows of one staged phase (MODE 0: x from global, MODE 2: x from the shared ring).
 template <typename T, int LANES, int MODE, bool RP>
 __device__ __forceinline__ void stage_rows(const SolveArgs<T> &a, const StageSlot<T> &s, int p0, int p1, int g, int G,
