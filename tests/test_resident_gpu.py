@@ -120,10 +120,32 @@ def test_resident_refusals_leave_the_plan_usable():
     assert rep["status"] == 0 and oracle.rel_error(x, oracle.solve(A, b[:, :1])[:, 0]) <= F64_TOL
 
 
-def test_resident_small_configuration_matches_oracle_bits_of_schedule():
+def test_resident_small_configuration():
     # the 64 x 64 configuration: one barrier per wavefront (127), x equal to the oracle's
     A, xs, b = W.config_small_2d()
     plan = sp.Plan(A)
     assert plan.stats()["levels"] == 127
     x, rep = _solve(plan, b, sync="resident")
     assert rep["status"] == 0 and oracle.rel_error(x, oracle.solve(A, b)[:, 0]) <= F64_TOL
+
+
+def test_resident_degenerate_factors():
+    # no off-diagonal entry at all (the bulk copies of columns and values are skipped)
+    A = W.from_pattern(5_000, [])
+    A.val[:] = np.linspace(0.5, 2.0, A.n)
+    b = np.random.default_rng(1).standard_normal((A.n, 1))
+    x, rep = _solve(sp.Plan(A), b, sync="resident")
+    assert rep["status"] == 0
+    assert np.max(np.abs(x - b[:, 0] / A.val) / np.abs(b[:, 0] / A.val)) <= 4.5e-16
+    # a single row
+    A1 = W.from_pattern(1, [])
+    A1.val[:] = 4.0
+    x1, rep = _solve(sp.Plan(A1), np.array([[2.0]]), sync="resident")
+    assert rep["status"] == 0 and x1.tolist() == [0.5]
+    # a chain: one row per phase (4096 phases, 32 walking threads)
+    n = 4096
+    Ab = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
+    xb, rep = _solve(sp.Plan(Ab), np.ones((n, 1)), sync="resident", threads=256)
+    assert rep["status"] == 0
+    # x_i = (1 + x_{i-1}) / 2 = 1 - 2^-(i+1): exact in FP64 while representable
+    assert np.allclose(xb, 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)

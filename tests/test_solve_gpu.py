@@ -202,7 +202,7 @@ def test_edge_sizes(n):
     A = W.from_pattern(n, [(i, i - 1) for i in range(1, n)], diag=2.0, off=-1.0)
     b = np.ones((n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta", "cta_regs", "local", "chunks"):
+    for sync in ("grid", "flags", "cta", "cta_regs", "local", "chunks", "resident"):
         x, rep = solve_gpu(plan, b, sync=sync)
         assert np.allclose(x[:, 0], 1.0 - 2.0 ** -(np.arange(n) + 1.0), rtol=0, atol=1e-15)
 
@@ -212,7 +212,7 @@ def test_diagonal_only_is_one_superstep():
     A.val[:] = np.linspace(0.5, 2.0, A.n)
     b = np.random.default_rng(0).standard_normal((A.n, 1))
     plan = sp.Plan(A)
-    for sync in ("grid", "flags", "cta", "local"):
+    for sync in ("grid", "flags", "cta", "local", "chunks"):
         x, rep = solve_gpu(plan, b, sync=sync)
         # x = b * (1/d): the reciprocal is rounded once on the host, so at most two roundings
         assert np.max(np.abs(x[:, 0] - b[:, 0] / A.val) / np.abs(b[:, 0] / A.val)) <= 4.5e-16
