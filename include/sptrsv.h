@@ -371,6 +371,18 @@ int sptrsv_solve(sptrsv_plan *plan, const void *b, void *x, int32_t nrhs, int64_
                  int32_t dtype, const sptrsv_solve_opts *opts, sptrsv_stream stream,
                  sptrsv_report *report);
 
+/* sptrsv_solve with b and x in HOST memory (Eq. 2.1 as above): b_host (column-major,
+ * leading dimension ld >= n) is copied into the plan's device staging buffer, the solve
+ * runs there, and x is copied back into x_host, all enqueued on `stream` in that order.
+ * Pinned host memory keeps the copies asynchronous; pageable memory works but the copies
+ * synchronise.  x_host holds the result once the stream has passed this call (report
+ * non-NULL: the call synchronises and fills it).  The staging buffer (2 n nrhs elements)
+ * is allocated on first use and kept with the plan.  Errors as sptrsv_solve, plus ARG
+ * for NULL host pointers. */
+int sptrsv_solve_host(sptrsv_plan *plan, const void *b_host, void *x_host, int32_t nrhs, int64_t ld,
+                      int32_t dtype, const sptrsv_solve_opts *opts, sptrsv_stream stream,
+                      sptrsv_report *report);
+
 /* Autotuner: time every candidate launch shape (sync mode x lanes per row x threads x
  * blocks per SM) of sptrsv_solve on the caller's b/x with CUDA events (x is overwritten),
  * remember the fastest in the plan for this (dtype, precision, nrhs class), and return it.

@@ -138,6 +138,8 @@ def lib():
                                                 ctypes.POINTER(vp)]),
             "sptrsv_destroy": (None, [vp]),
             "sptrsv_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+            "sptrsv_solve_host": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
+                                                 ctypes.POINTER(Report)]),
             "sptrsv_solve": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
                                             ctypes.POINTER(Report)]),
             "sptrsv_autotune": (ctypes.c_int, [vp, vp, vp, i32, i64, i32, ctypes.POINTER(SolveOpts), vp,
@@ -383,6 +385,29 @@ class Plan:
         if x is not None and (x.dtype != b.dtype or x.shape != b.shape or x.stride() != b.stride()):
             raise ValueError("x must match b in dtype, shape and strides")
         return nrhs, ld, dtype
+
+    def solve_host(self, b, x=None, *, stream=None, report=True, **opts):
+        """Solve with ``b`` and ``x`` in host memory (CPU tensors, float64 or float32, (n,) or
+        (n, nrhs) column-major; pinned memory keeps the copies asynchronous): the library
+        copies b in, solves and copies x out on the stream (``sptrsv_solve_host``)."""
+        import torch
+        if b.is_cuda or (x is not None and x.is_cuda):
+            raise TypeError("solve_host takes CPU tensors")
+        dtype = F64 if b.dtype == torch.float64 else F32 if b.dtype == torch.float32 else None
+        if dtype is None:
+            raise TypeError("b must be float64 or float32")
+        nrhs, ld = _colmajor_info(b, self.n)
+        if x is None:
+            x = torch.empty_strided(b.shape, b.stride(), dtype=b.dtype).pin_memory()
+        if x.dtype != b.dtype or _colmajor_info(x, self.n) != (nrhs, ld):
+            raise ValueError("x must match b in dtype, shape and leading dimension")
+        rep = Report()
+        o = solve_opts(**opts)
+        st = lib().sptrsv_solve_host(self.handle, _ptr(b), _ptr(x), int(nrhs), int(ld), dtype,
+                                     ctypes.byref(o), _stream_handle(stream),
+                                     ctypes.byref(rep) if report else None)
+        _check(st)
+        return x, (rep.as_dict() if report else None)
 
     def solve(self, b, x=None, *, stream=None, report=True, **opts):
         """Solve L x = b for a CUDA tensor ``b`` of shape (n,) or (n, nrhs) column-major

@@ -155,7 +155,7 @@ void free_device(sptrsv_plan *p) {
     void *ptrs[] = {d.rp,       d.col,      d.val,       d.dinv,      d.val_hi,    d.val_lo, d.diag_hi,
                     d.diag_lo,  d.dinv32,   d.s32,       d.perm,      d.step_blk,  d.blk_phase, d.phase_row,
                     d.phase_ent,
-                    d.counters, d.flags,    d.work,
+                    d.counters, d.flags,    d.work,      d.io,
                     d.l_rp,     d.l_col,    d.l_perm,    d.l_blk_row, d.l_val,     d.l_dinv, d.l_s32,
                     d.l_dinv32,
                     d.ck_info,  d.ck_blk,   d.ck_col,    d.ck_orow,   d.ck_val,    d.ck_dinv, d.ck_s32,
@@ -1154,6 +1154,49 @@ int sptrsv_solve(sptrsv_plan *p, const void *b, void *x, int32_t nrhs, int64_t l
     LaunchCfg c{};
     st = solve_impl(p, b, x, nrhs, ld, dtype, o, s, c);
     if (st) return st;
+    if (report) return read_report(p, c, s, report, dtype == SPTRSV_F64 && o.precision == SPTRSV_PREC_F32_REFINE, o);
+    return SPTRSV_OK;
+}
+
+int sptrsv_solve_host(sptrsv_plan *p, const void *b_host, void *x_host, int32_t nrhs, int64_t ld, int32_t dtype,
+                      const sptrsv_solve_opts *opts, sptrsv_stream stream, sptrsv_report *report) {
+    clear_error();
+    if (!b_host || !x_host) return fail(SPTRSV_ERR_ARG, "host buffers must not be NULL");
+    if (!p) return fail(SPTRSV_ERR_ARG, "plan is NULL");
+    if (dtype != SPTRSV_F64 && dtype != SPTRSV_F32) return fail(SPTRSV_ERR_ARG, "dtype must be F64 or F32");
+    if (nrhs < 0 || (nrhs > 0 && ld < std::max<int64_t>(p->h.n, 1)))
+        return fail(SPTRSV_ERR_ARG, "nrhs must be >= 0 and ld >= n");
+    if (p->device < 0) return fail(SPTRSV_ERR_NO_DEVICE, "plan has no device copy");
+    if (p->h.n == 0 || nrhs == 0) {
+        if (report) std::memset(report, 0, sizeof(*report));
+        return SPTRSV_OK;
+    }
+    DeviceGuard g(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t es = dtype == SPTRSV_F64 ? sizeof(double) : sizeof(float);
+    const size_t n = size_t(p->h.n), vec = (n * size_t(nrhs) * es + 255) & ~size_t(255);
+    if (p->d.io_bytes < 2 * vec) {
+        if (p->d.io) {
+            CUDA_TRY(cudaFree(p->d.io));
+            p->device_bytes -= int64_t(p->d.io_bytes);
+            p->d.io = nullptr;
+            p->d.io_bytes = 0;
+        }
+        CUDA_TRY(cudaMalloc(&p->d.io, 2 * vec));
+        p->d.io_bytes = 2 * vec;
+        p->device_bytes += int64_t(2 * vec);
+    }
+    char *bd = static_cast<char *>(p->d.io), *xd = bd + vec;
+    CUDA_TRY(cudaMemcpy2DAsync(bd, n * es, b_host, size_t(ld) * es, n * es, size_t(nrhs), cudaMemcpyHostToDevice, s));
+    sptrsv_solve_opts o;
+    sptrsv_solve_opts_default(&o);
+    if (opts) o = *opts;
+    int st = check_solve_args(p, bd, xd, nrhs, int64_t(n), dtype, o);
+    if (st) return st;
+    LaunchCfg c{};
+    st = solve_impl(p, bd, xd, nrhs, int64_t(n), dtype, o, s, c);
+    if (st) return st;
+    CUDA_TRY(cudaMemcpy2DAsync(x_host, size_t(ld) * es, xd, n * es, n * es, size_t(nrhs), cudaMemcpyDeviceToHost, s));
     if (report) return read_report(p, c, s, report, dtype == SPTRSV_F64 && o.precision == SPTRSV_PREC_F32_REFINE, o);
     return SPTRSV_OK;
 }

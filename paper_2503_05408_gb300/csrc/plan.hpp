@@ -73,6 +73,8 @@ struct DeviceBuffers {
     uint32_t *flags = nullptr;    // n ready flags holding the solve epoch
     void *work = nullptr;         // refinement / internal vectors (grown on demand)
     size_t work_bytes = 0;
+    void *io = nullptr;           // host-buffer solves: device copies of b and x (grown on demand)
+    size_t io_bytes = 0;
     // block-local executor layout (built on first use for loc_nb thread blocks):
     // rows block-major, each block's rows in (wavefront, id) order; a column id
     // c >= 0 is an original row id (parent of another block), c <= -2 names the

@@ -475,3 +475,44 @@ def test_saved_plan_with_local_partition(tmp_path, name, tri):
     assert rep["status"] == 0 and oracle.rel_error(x4, xo) <= F64_TOL
     x3, rep = solve_gpu(loaded, b, sync="flags")
     assert rep["status"] == 0 and oracle.rel_error(x3, xo) <= F64_TOL
+
+
+@pytest.mark.parametrize("sync", ["chunks", "resident", "flags", "cta"])
+def test_solve_host_buffers_match_device_call(sync):
+    # sptrsv_solve_host: b copied in, the solve, x copied out, all by the library
+    A = SMALL["lap2d_64x64"]()
+    xs, b = W.manufactured_rhs(A, 1, seed=71)
+    plan = sp.Plan(A)
+    bh = torch.from_numpy(np.ascontiguousarray(b[:, 0])).pin_memory()
+    xh, rep = plan.solve_host(bh, sync=sync)
+    assert rep["status"] == 0 and not xh.is_cuda
+    assert oracle.rel_error(xh.numpy(), oracle.solve(A, b)[:, 0]) <= F64_TOL
+    xd, _ = plan.solve(bh.cuda(), sync=sync)
+    if sync == "flags":     # sums in arrival order: the last bits may differ from run to run
+        assert oracle.rel_error(xh.numpy(), xd.cpu().numpy()) <= F64_TOL
+    else:                   # a fixed order per row: the same bits as the device-buffer call
+        assert np.array_equal(xh.numpy(), xd.cpu().numpy())
+
+
+def test_solve_host_buffers_padded_pageable_and_refined():
+    A = SMALL["random_60k"]()
+    n, r, ld = A.n, 3, A.n + 5
+    xs, b = W.manufactured_rhs(A, r, seed=72)
+    xo = oracle.solve(A, b)
+    plan = sp.Plan(A)
+    buf = torch.zeros((r, ld), dtype=torch.float64)                    # pageable, padded
+    buf[:, :n] = torch.from_numpy(np.ascontiguousarray(b.T))
+    bh = buf.T[:n]
+    xbuf = torch.full((r, ld), float("nan"), dtype=torch.float64)
+    xh = xbuf.T[:n]
+    _, rep = plan.solve_host(bh, xh, sync="flags", lanes=4)
+    assert rep["status"] == 0 and oracle.rel_error(xh.numpy(), xo) <= F64_TOL
+    assert torch.isnan(xbuf[:, n:]).all()                               # the padding is untouched
+    x1 = torch.empty(n, dtype=torch.float64).pin_memory()
+    _, rep = plan.solve_host(bh[:, 0].contiguous().pin_memory(), x1, precision="f32_refine")
+    assert rep["status"] == 0 and rep["berr"] <= 1e-13
+    assert oracle.rel_error(x1.numpy(), xo[:, 0]) <= F64_TOL
+    x32, rep = plan.solve_host(bh[:, 0].contiguous().float())
+    assert rep["status"] == 0 and oracle.rel_error(x32.double().numpy(), xo[:, 0]) <= 1e-4
+    with pytest.raises(TypeError):
+        plan.solve_host(bh.cuda())
