@@ -131,32 +131,79 @@ __device__ double item_residual(const BatchItem &it, bool zero_x, double &bm, do
     const double *b = static_cast<const double *>(it.b);
     const double *x = static_cast<const double *>(it.x);
     double rm = 0.0, bmax = 0.0;
-    for (int r = threadIdx.x; r < it.n; r += blockDim.x) {
-        const int o = __ldg(it.perm + r);
-        const int beg = __ldg(it.rp + r), end = __ldg(it.rp + r + 1);
-        const double dh = __ldg(it.dhi + r), dl = __ldg(it.dlo + r);
-        const double d = dh + dl;
-        for (int j = 0; j < it.nrhs; ++j) {
-            double s = b[o + (int64_t)j * it.ldb];
-            bmax = max_abs_bits(bmax, s);        // integer compare: keeps the FP64 pipe for the sums
-            if (!zero_x && it.val) {
-                const double *xj = x + (int64_t)j * it.ldx;
-                double sum = xj[o];
-                for (int q = beg; q < end; ++q) sum = fma(__ldg(it.val + q), xj[__ldg(it.col + q)], sum);
-                s = fma(-d, sum, s);
-            } else if (!zero_x) {
-                const double *xj = x + (int64_t)j * it.ldx;
-                for (int q = beg; q < end; ++q) {
-                    const double xv = xj[__ldg(it.col + q)];
-                    s = fma(-double(__ldg(it.hi + q)), xv, s);
-                    s = fma(-double(__ldg(it.lo + q)), xv, s);
-                }
-                const double xo = xj[o];
-                s = fma(-dh, xo, s);
-                s = fma(-dl, xo, s);
+    // Four rows per thread and round, their row data and (rows of at most four entries)
+    // columns and values read up front, so each right-hand side's gathers of x for the
+    // four rows are in flight together: one block walks the whole factor here, and a
+    // row at a time it waits a memory round trip per row.
+    constexpr int RU = 4, EU = 4;
+    const int nt = blockDim.x;
+    for (int r0 = threadIdx.x; r0 < it.n; r0 += nt * RU) {
+        int o[RU], beg[RU], len[RU];
+        double dh[RU], dl[RU];
+        int cc[RU][EU];
+        double vv[RU][EU];
+#pragma unroll
+        for (int k = 0; k < RU; ++k) {
+            const int r = r0 + k * nt;
+            const bool has = r < it.n;
+            o[k] = has ? __ldg(it.perm + r) : -1;
+            beg[k] = has ? __ldg(it.rp + r) : 0;
+            len[k] = has ? __ldg(it.rp + r + 1) - beg[k] : 0;
+            dh[k] = has ? double(__ldg(it.dhi + r)) : 0.0;
+            dl[k] = has ? double(__ldg(it.dlo + r)) : 0.0;
+        }
+        const bool fast = it.val != nullptr;
+#pragma unroll
+        for (int k = 0; k < RU; ++k)
+#pragma unroll
+            for (int u = 0; u < EU; ++u) {
+                const bool e = fast && u < len[k] && len[k] <= EU;
+                cc[k][u] = e ? __ldg(it.col + beg[k] + u) : 0;
+                vv[k][u] = e ? __ldg(it.val + beg[k] + u) : 0.0;
             }
-            it.r32[o + (int64_t)j * it.n] = float(s);
-            rm = max_abs_bits(rm, s);
+        for (int j = 0; j < it.nrhs; ++j) {
+            const double *xj = x + (int64_t)j * it.ldx;
+            double s[RU], sum[RU];
+#pragma unroll
+            for (int k = 0; k < RU; ++k) {
+                s[k] = o[k] >= 0 ? b[o[k] + (int64_t)j * it.ldb] : 0.0;
+                sum[k] = (!zero_x && fast && o[k] >= 0) ? xj[o[k]] : 0.0;
+            }
+            if (!zero_x) {
+#pragma unroll
+                for (int k = 0; k < RU; ++k) {
+                    if (o[k] < 0) continue;
+                    if (fast && len[k] <= EU) {
+                        double xv[EU];
+#pragma unroll
+                        for (int u = 0; u < EU; ++u) xv[u] = u < len[k] ? xj[cc[k][u]] : 0.0;
+#pragma unroll
+                        for (int u = 0; u < EU; ++u)
+                            if (u < len[k]) sum[k] = fma(vv[k][u], xv[u], sum[k]);
+                        s[k] = fma(-(dh[k] + dl[k]), sum[k], s[k]);
+                    } else if (fast) {
+                        for (int q = beg[k]; q < beg[k] + len[k]; ++q)
+                            sum[k] = fma(__ldg(it.val + q), xj[__ldg(it.col + q)], sum[k]);
+                        s[k] = fma(-(dh[k] + dl[k]), sum[k], s[k]);
+                    } else {                   // FP32 values only: the hi + lo split
+                        for (int q = beg[k]; q < beg[k] + len[k]; ++q) {
+                            const double xv = xj[__ldg(it.col + q)];
+                            s[k] = fma(-double(__ldg(it.hi + q)), xv, s[k]);
+                            s[k] = fma(-double(__ldg(it.lo + q)), xv, s[k]);
+                        }
+                        const double xo = xj[o[k]];
+                        s[k] = fma(-dh[k], xo, s[k]);
+                        s[k] = fma(-dl[k], xo, s[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < RU; ++k) {
+                if (o[k] < 0) continue;
+                bmax = max_abs_bits(bmax, b[o[k] + (int64_t)j * it.ldb]);
+                it.r32[o[k] + (int64_t)j * it.n] = float(s[k]);
+                rm = max_abs_bits(rm, s[k]);
+            }
         }
     }
     bm = block_max(bmax, s_scratch);
