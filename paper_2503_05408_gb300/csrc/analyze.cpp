@@ -338,7 +338,7 @@ bool grid_partition(int32_t n, int32_t nb, int32_t row_cap, const std::vector<in
     return true;
 }
 
-// A saved schedule is accepted only if the executors can run it// A saved schedule is accepted only if the executors can run it: supersteps
+// A saved schedule is accepted only if the executors can run it: supersteps
 // 0..S-1 all used, cores in [0, k), every edge into a later superstep or inside
 // one core's block (Def. 2.1); a wavefront schedule must be the wavefronts.
 int check_given(const sptrsv_csr *A, const HostSchedule &h, const GivenSchedule &g) {
